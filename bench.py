@@ -1,0 +1,360 @@
+"""Benchmark of batched complex beamforming R = W x S on GB300 (one JSON line).
+
+Workload: the full-band f = 36 case -- 273 resource blocks x 14 OFDM symbols
+= 3,822 blocks of S (36 x 60, 64-QAM, complex64), one 64 x 36 unit-column
+precoder per resource block shared by its 14 symbols; R is 64 x 60 complex64
+per block. A step is one pass of the product over the whole batch: one
+graph-captured persistent launch of the best form (split-bf16 on the tensor
+cores, complex64 in and out). Three buffer sets (S, R) rotate so that the
+working set (565 MB) is well above the 129 MB L2 between steps.
+
+Reported beside the headline: blocks/s, the plain FP32 CUDA-core form on the
+same GPU, the end-to-end rate through the host-buffer entry point, the
+roofline of the dominant kernel, GPU clocks during the timed region, the
+accuracy of the timed output against the FP64 oracle, and the oracle's own
+CPU rate (the oracle is only run in that CPU-baseline leg).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs the same workload on its own GPU (weak scaling,
+no data exchange; rank 0 prints).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+METRIC = "complex GFLOP/s & blocks/s for W×S at f=36 vs FP32 plain; p99 TTI latency"
+UNIT = "GFLOP/s"
+WORKLOAD = "fullband f=36, 273 RB x 14 symbols = 3,822 blocks, W 64x36 per RB, S 36x60 64-QAM, complex64 in/out"
+L2_NOTE = "3 rotating buffer sets of S and R (565 MB > 2x the 129 MB L2)"
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def traffic_for(kernel_src: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_1810_11451_gb300", "csrc", kernel_src)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"bf_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.out):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.out) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, dist.get_rank(), world
+    return None, 0, 1
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(batch, budget_s: float = 12.0):
+    """Time the FP64 oracle, as it stands, on the host cores over the whole
+    workload, repeated until about budget_s of CPU time; also returns its R."""
+    import oracle
+    oracle.lib()
+    rb = batch.rounded(np.complex64)
+    t0 = time.perf_counter()
+    reps, ref = 0, None
+    while True:
+        ref = oracle.apply_batch(rb)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    gflops = batch.flops() * reps / dt / 1e9
+    return {"value": gflops, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the whole workload ({batch.total_blocks} blocks) x {reps} repetitions, {dt:.1f} s, FP64"}, ref
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores on this workload."""
+    dist, rank, world = dist_init()
+    if rank != 0:
+        return
+    import workloads as wl
+    import oracle
+    batch = wl.config_fullband()
+    rb = batch.rounded(np.complex64)
+    oracle.lib()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.warmup)):
+        oracle.apply_blocks(rb.W[0], rb.S[0])
+    t_rb = (time.perf_counter() - t0) / max(1, args.warmup)
+    # each step: a bounded sample of the workload (its first n_rb resource blocks),
+    # sized so that all steps together take about a minute
+    n_rb = int(max(1, min(len(rb.S), (60.0 / max(1, args.steps)) / max(t_rb, 1e-6))))
+    sample = type(batch)(rb.W, rb.prec[:n_rb], rb.S[:n_rb], rb.name)
+    desc = f"first {n_rb} of 273 resource blocks ({n_rb * 14} blocks) per step"
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply_batch(sample)
+    dt = time.perf_counter() - t0
+    v = sample.flops() * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_graphs(torch, bf, handles, steps, warmup, stream):
+    for i in range(warmup):
+        bf.bf_batch_launch(handles[i % len(handles)], stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        bf.bf_batch_launch(handles[i % len(handles)], stream)
+        ev[i][1].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(stop)
+    per = [a.elapsed_time(b) for a, b in ev]
+    return total_ms, per
+
+
+def end_to_end(torch, bf, plan, Sflat, lay, r_numel, stream, dist, world, flops, steps=20):
+    """The same product through bf_apply_batch_host: S copied in from pinned
+    host memory and R copied out, every step, inside the timed region."""
+    S_h = torch.from_numpy(np.ascontiguousarray(Sflat.astype(np.complex64)).view(np.float32).copy()).pin_memory()
+    R_h = torch.empty(r_numel, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        bf.bf_apply_batch_host(plan, S_h, lay.groups, bf.BF_BF16X3, R_h, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        bf.bf_apply_batch_host(plan, S_h, lay.groups, bf.BF_BF16X3, R_h, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1) / steps)
+    return {"value": world * flops / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": int(lay.s_bytes), "d2h_bytes_per_step": int(lay.r_blocks * 30720)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain leg")
+    ap.add_argument("--sets", type=int, default=3, help="rotating buffer sets (3 keeps the working set above L2)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1810_11451_gb300 as bf
+    import workloads as wl
+    from bfrun import layout, set_precoders, to_device_c64
+
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    plan = bf.bf_plan_create(64, 36, 60)
+    batch = wl.config_fullband()
+    set_precoders(plan, batch, torch)
+    lay = layout(batch)
+    Sflat, _ = batch.pack_S()
+    n_sets = max(1, args.sets)
+    S_sets = [to_device_c64(Sflat, torch) for _ in range(n_sets)]
+    R_sets = [torch.empty(lay.r_blocks * 64 * 60 * 2, dtype=torch.float32, device="cuda") for _ in range(n_sets)]
+    stream = torch.cuda.current_stream()
+    best = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_BF16X3, R_sets[s]) for s in range(n_sets)}
+    plain = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_FP32, R_sets[s]) for s in range(n_sets)}
+    handles = [best[s] for s in range(n_sets)]
+    flops = batch.flops()
+    alg_bytes = batch.algorithmic_bytes()
+
+    # ---- headline: best form, device-resident inputs
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = bf.bf_plan_launch_count(plan)
+    with ClockSampler(local) as clk:
+        total_ms, per = time_graphs(torch, bf, handles, args.steps, args.warmup, stream)
+    launches = bf.bf_plan_launch_count(plan) - launches0 - args.warmup
+    barrier(dist)
+    total_ms = max_over_ranks(dist, total_ms)
+    ms_step = total_ms / args.steps
+    kern_ms = statistics.mean(per)
+    value = world * flops * args.steps / (total_ms * 1e-3) / 1e9
+    blocks_s = world * batch.total_blocks * args.steps / (total_ms * 1e-3)
+
+    # ---- the plain FP32 form on the same GPU
+    k2 = max(50, args.steps // 10)
+    p_ms, p_per = float("nan"), [float("nan")]
+    if not args.no_plain:
+        p_total, p_per = time_graphs(torch, bf, [plain[s] for s in range(n_sets)], k2, args.warmup, stream)
+        p_ms = p_total / k2
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, bf, plan, Sflat, lay, R_sets[0].numel(), stream, dist, world, flops)
+
+    # ---- CPU baseline (oracle) and the accuracy of the timed output
+    cpu, acc = None, None
+    if rank == 0 and not args.no_cpu:
+        cpu, ref = cpu_baseline(batch)
+        Rref = np.concatenate([r.reshape(-1) for r in ref])
+        Rref_d = torch.from_numpy(Rref.view(np.float64)).cuda()
+        for name, h in (("bf16x3", best[0]), ("fp32", plain[0])):
+            bf.bf_batch_launch(h, stream)
+            num, den = bf.bf_errnorm(plan, R_sets[0], Rref_d, lay.r_blocks, None, stream)
+            acc = acc or {}
+            acc[name] = float(np.sqrt(num / den))
+    status = bf.bf_device_status(plan)
+    
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "split-bf16 (hi*hi + hi*lo + lo*hi) tcgen05, FP32 accumulate",
+                   "blocks": batch.total_blocks, "l2": L2_NOTE, "launch": "one graph-captured persistent kernel",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "blocks_per_s": blocks_s,
+        "fp32_plain": {"value": world * flops / (p_ms * 1e-3) / 1e9 if p_ms == p_ms else None, "unit": UNIT, "ms_per_step": p_ms,
+                       "kernel_ms": statistics.mean(p_per),
+                       "blocks_per_s": world * batch.total_blocks / (p_ms * 1e-3)},
+        "speedup_vs_fp32_plain": p_ms / ms_step if p_ms == p_ms else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_for("bf_tc.cu"),
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "bf_tc_kernel<3,false,true>",
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "accuracy_rel_frobenius": acc,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "device_status": bf.bf_status_string(status),
+    }
+    for s in range(n_sets):
+        bf.bf_batch_destroy(best[s])
+        bf.bf_batch_destroy(plain[s])
+    bf.bf_plan_destroy(plan)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * bf.h -- C ABI of libbf, batched complex beamforming R = W x S on GB300 (sm_103a).
+ *
+ * The operation (Sec. III, beamforming equation and the sentences around it):
+ * a precoding matrix W with one row per antenna (n_ant = 64, Sec. II) and f
+ * columns, one per parallel flow (0 <= f <= 36), is applied to many symbol
+ * blocks S of f rows by b = 60 resource elements; W stays constant while S
+ * changes. Each block gives R = W x S (n_ant x b), i.e. for every antenna i
+ *     R[i][j] = sum_{k<f} W[i][k] * S[k][j],   j < b.
+ * f = 0 gives R = 0.
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are interleaved (re, im) FP32 pairs ("complex64").
+ *  - W is row-major n_ant x f (antenna-major); an S block is row-major f x b
+ *    (flow-major, b = 60 contiguous complex per flow); an R block is row-major
+ *    n_ant x b. A block of S is 480*f bytes, a block of R 30,720 bytes.
+ *  - Blocks that share a precoder form a group and are contiguous in S and R.
+ *  - "_dev" pointers are CUDA device pointers (e.g. from PyTorch), "_host"
+ *    pointers are host memory. The caller owns every buffer it passes; the
+ *    library never frees or keeps them past the call except where stated.
+ *  - Device buffers and byte offsets must be 16-byte aligned (BF_EINVAL).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    take a stream are asynchronous on it unless stated otherwise.
+ *  - Every call returns a bf_status and never aborts or exits. The text of the
+ *    last error of a plan is in bf_last_error(plan).
+ *  - A plan is not thread-safe: one host thread at a time per plan (the
+ *    serving engine serialises its own use internally).
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_EINVAL = 1,     /* an argument is out of range, NULL or misaligned      */
+    BF_ENOMEM = 2,     /* device or host allocation failed                      */
+    BF_EBUDGET = 3,    /* a serving job is larger than the whole HBM budget     */
+    BF_ECUDA = 4,      /* a CUDA runtime call failed (text in bf_last_error)   */
+    BF_ETIMEOUT = 5,   /* a bounded device or host wait gave up                */
+    BF_EAGAIN = 6,     /* the serving queue is full; try again                  */
+    BF_EBUSY = 7,      /* the object still has work in flight                   */
+    BF_ENOTREADY = 8,  /* the result is not available yet                       */
+    BF_ENOTFOUND = 9   /* unknown ticket / unset precoder slot                  */
+} bf_status;
+
+/* Arithmetic of the product. All forms accumulate in FP32 and write complex64 R.
+ *  BF_FP32   : plain form, FP32 fused multiply-add on the CUDA cores; S complex64.
+ *  BF_BF16   : single-pass tensor-core form, operands rounded to bfloat16.
+ *  BF_FP16   : single-pass tensor-core form, operands rounded to binary16.
+ *  BF_BF16X3 : split form, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
+ *              R = Wh*Sh + Wh*Sl + Wl*Sh on the tensor cores.
+ * The tensor-core forms take S either as complex64 (converted on chip, no
+ * per-block scale) or "held": pre-encoded by bf_quantize_symbols with one
+ * power-of-two scale per block. W is always taken from the plan's images. */
+typedef enum { BF_FP32 = 0, BF_BF16 = 1, BF_FP16 = 2, BF_BF16X3 = 3 } bf_precision;
+
+/* One group: n_blocks consecutive blocks that all multiply precoder prec_id.
+ * s_off / r_off are BYTE offsets of the group's first block in the S and R
+ * buffers (multiples of 16). For complex64 S, block n of the group starts at
+ * s_off + n*480*f; for held S at s_off + n*bf_held_block_bytes(f, prec).
+ * R block n starts at r_off + n*30720. */
+typedef struct {
+    int32_t prec_id;
+    int32_t n_blocks;
+    int64_t s_off;
+    int64_t r_off;
+} bf_group;
+
+typedef struct bf_plan_s *bf_plan;
+
+/* ------------------------------------------------------------------ plan */
+
+/* Create a plan on the current CUDA device. The kernels are built for the
+ * paper's shapes: n_ant must be 64, b must be 60 and 0 <= f_max <= 36
+ * (Sec. III). Returns BF_EINVAL for other shapes (checked before any CUDA
+ * call), BF_ECUDA if there is no usable sm_103 device. *out receives the plan.
+ * The plan owns the precoder images, its work-list buffers, captured graphs,
+ * the autotune table and its device status word. */
+bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out);
+
+/* Free the plan and everything it owns. Synchronises the device first.
+ * NULL is accepted (BF_OK). */
+bf_status bf_plan_destroy(bf_plan plan);
+
+/* Human-readable text of the plan's last error ("" if none). Valid until the
+ * next call on the plan. A NULL plan gives the last plan-less error (creation). */
+const char *bf_last_error(bf_plan plan);
+
+/* Static name of a status code. */
+const char *bf_status_string(bf_status s);
+
+/* Reads and clears the plan's device status word, which kernels set when a
+ * bounded on-chip wait gives up (they then stop early, leaving R incomplete).
+ * Synchronises the device. BF_OK or BF_ETIMEOUT. */
+bf_status bf_device_status(bf_plan plan);
+
+/* ------------------------------------------------------------------ precoders */
+
+/* Set precoder slots first_id .. first_id+n_prec-1 (Sec. III: W is constant
+ * across many S, so it is converted once here and reused).
+ *  W_dev  : n_prec precoders packed back to back, precoder p row-major
+ *           n_ant x f_host[p] complex64 (device, 8-byte aligned).
+ *  f_host : f of each precoder, 0 <= f <= f_max.
+ * Builds, on `stream`, every device image the kernels read: planar FP32,
+ * bfloat16 hi/lo and binary16 in the tensor cores' shared-memory layout, with
+ * a power-of-two scale per precoder (2^ceil(log2 max(|Re|,|Im|))). Slots grow
+ * on demand; growing synchronises the device. Later launches that read these
+ * slots must be ordered after `stream`. W_dev may be freed once `stream` has
+ * passed this call. */
+bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_host,
+                           int32_t n_prec, int32_t first_id, void *stream);
+
+/* ------------------------------------------------------------------ held symbols */
+
+/* Bytes of one held (pre-encoded) S block for precision prec at f flows:
+ * terms * 128 * K, K = 2f rounded up to a multiple of 16, terms = 2 for
+ * BF_BF16X3 and 1 for BF_BF16 / BF_FP16; 0 for BF_FP32 or f out of range.
+ * Layout of a term: 64 rows (resource element j; rows 60..63 are zero) by K
+ * columns (column 2k = Re S[k][j], 2k+1 = Im S[k][j], zero beyond 2f), stored
+ * as 8x8 tiles of 16-bit values: element (row, col) at byte
+ * (row/8)*16*K + (col/8)*128 + (row%8)*16 + (col%8)*2. For BF_BF16X3 the hi
+ * term comes first, then the lo term. */
+int64_t bf_held_block_bytes(int f, bf_precision prec);
+
+/* Encode complex64 S blocks for a tensor-core precision ("held" S).
+ *  S_dev      : complex64 S; group g's blocks at groups[g].s_off (bytes).
+ *  q_off_host : per group, the byte offset of its first held block in Sq_dev
+ *               (multiple of 16); its blocks follow at bf_held_block_bytes.
+ *  scale_dev  : one float per block, in group order (block n of group g at
+ *               index sum_{h<g} n_blocks[h] + n): the power of two that the
+ *               encoded values are multiplied by to give S back.
+ * Per block: scale = 2^ceil(log2 m), m = max over the block of |Re| and |Im|
+ * (1 when m = 0); each value x/scale is rounded to nearest even in the target
+ * format; BF_BF16X3 stores hi = bf16(x/scale) and lo = bf16(x/scale - hi). */
+bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const bf_group *groups,
+                              int32_t n_groups, bf_precision prec, void *Sq_dev,
+                              const int64_t *q_off_host, float *scale_dev, void *stream);
+
+/* ------------------------------------------------------------------ the product */
+
+/* R = W x S for every block of every group, in one persistent launch on
+ * `stream` (Sec. III).
+ *  S_dev     : complex64 S (scale_dev == NULL) or held S from
+ *              bf_quantize_symbols (scale_dev != NULL; BF_BF16, BF_FP16 and
+ *              BF_BF16X3 only). Group offsets as in bf_group.
+ *  groups    : host array, read during the call only.
+ *  R_dev     : complex64 R; every element of every listed block is written
+ *              (zeros for f = 0).
+ * The host builds a work list (tiles of up to two blocks of one group, each
+ * CTA a cost-balanced run of tiles) and uploads it to a plan-owned buffer;
+ * the launch then reads it. Calls on one plan must not overlap in host
+ * threads; launches on different streams may overlap on the device only if
+ * each call's work list is not still being read, which the plan guarantees by
+ * keeping one work-list buffer per call in flight (a ring; the oldest is
+ * reused after its launch has completed). */
+bf_status bf_apply_batch(bf_plan plan, const void *S_dev, const float *scale_dev,
+                         const bf_group *groups, int32_t n_groups, bf_precision prec,
+                         void *R_dev, void *stream);
+
+/* The same product with S and R in HOST memory (best pinned). S is copied in,
+ * the product runs, R is copied out, pipelined in chunks of groups over two
+ * internal streams so that copies overlap the kernels. Ordered after
+ * `stream`; `stream` is ordered after its completion (synchronise `stream`
+ * before reading R_host). Group offsets refer to the host buffers. */
+bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups,
+                              int32_t n_groups, bf_precision prec, void *R_host,
+                              void *stream);
+
+/* A prepared batch: the work list is built and uploaded once and the launch
+ * is captured in a CUDA graph, so bf_batch_launch is a single graph replay.
+ * Arguments as bf_apply_batch; the buffers must stay valid for the batch's
+ * lifetime. */
+typedef struct bf_batch_s *bf_batch;
+bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev,
+                          const bf_group *groups, int32_t n_groups, bf_precision prec,
+                          void *R_dev, bf_batch *out);
+bf_status bf_batch_launch(bf_batch batch, void *stream);
+bf_status bf_batch_destroy(bf_batch batch);
+
+/* ------------------------------------------------------------------ scheduler */
+
+/* One work item of a launch: up to two consecutive blocks of one group. */
+typedef struct {
+    int64_t s_off;       /* byte offset of the first block in S                  */
+    int64_t r_off;       /* byte offset of the first block in R                  */
+    int32_t prec_id;     /* precoder slot                                        */
+    int32_t first_block; /* index of the first block in group order              */
+    int16_t f;           /* flows of the precoder                                */
+    int16_t n_blocks;    /* 1 or 2                                               */
+    int32_t flags;       /* 1: first tile of its precoder in its CTA's run;
+                            2: last such tile (tiles with f > 0 only)            */
+} bf_tile;
+
+/* The work-list scheduler that bf_apply_batch runs on the host, exposed as a
+ * pure host function (no CUDA call). The groups (Sec. III: many S per
+ * constant W) are cut into tiles of up to two blocks, in group order, and the
+ * tiles are split into at most max_cta contiguous runs of about equal cost
+ * (bytes of S read and R written, optionally weighted per f by the autotune
+ * table; here the weights are 1), one run per CTA, so each CTA loads a
+ * precoder once per run.
+ *  f_of_slot : f of each precoder slot (n_slots entries).
+ *  tiles_out : NULL to query the tile count; else room for max_tiles tiles.
+ *  cta_begin_out : room for max_cta + 1 entries; CTA c runs tiles
+ *                  [cta_begin_out[c], cta_begin_out[c+1]).
+ *  *n_cta_out receives the number of CTAs.
+ * Returns the number of tiles, or -BF_EINVAL. */
+int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *groups, int32_t n_groups,
+                    bf_precision prec, int32_t held, int32_t max_cta, bf_tile *tiles_out,
+                    int32_t max_tiles, int32_t *cta_begin_out, int32_t *n_cta_out);
+
+/* ------------------------------------------------------------------ accuracy report */
+
+/* Relative Frobenius error of R against a reference, accumulated in FP64.
+ *  R_dev    : n_blocks blocks of complex64 R (30,720 B each).
+ *  Rref_dev : the same blocks as complex128 (FP64 pairs, 61,440 B each).
+ *  per_block_dev : NULL or 2*n_blocks doubles receiving, per block,
+ *                  sum |R-Rref|^2 and sum |Rref|^2.
+ *  total_host    : 2 doubles receiving the totals over all blocks.
+ * Synchronises `stream` (the totals are copied to the host). */
+bf_status bf_errnorm(bf_plan plan, const void *R_dev, const void *Rref_dev, int64_t n_blocks,
+                     double *per_block_dev, double *total_host, void *stream);
+
+/* Number of product kernels (or graph replays) this plan has launched so far
+ * (0 for a NULL plan). */
+int64_t bf_plan_launch_count(bf_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_H */

@@ -1,0 +1,241 @@
+"""Python binding of libbf: batched complex beamforming R = W x S on GB300.
+
+A thin ctypes layer over the C ABI in `include/bf.h`: every function here has
+the C function's name and only marshals arguments (tensors become device or
+host pointers via `data_ptr()`, streams become `cudaStream_t` handles). All
+arithmetic runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and importing a function that needs the library raises when
+`libbf.so` has not been built (`python -m paper_1810_11451_gb300.build`).
+
+Statuses other than BF_OK raise `BfError` carrying the status and the plan's
+`bf_last_error` text.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
+from typing import Iterable, Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbf.so")
+
+# bf_status
+BF_OK, BF_EINVAL, BF_ENOMEM, BF_EBUDGET, BF_ECUDA, BF_ETIMEOUT, BF_EAGAIN, BF_EBUSY, \
+    BF_ENOTREADY, BF_ENOTFOUND = range(10)
+# bf_precision
+BF_FP32, BF_BF16, BF_FP16, BF_BF16X3 = range(4)
+PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "fp16": BF_FP16, "bf16x3": BF_BF16X3}
+
+N_ANT, B_RE, F_LIMIT = 64, 60, 36
+S_BYTES_PER_F = B_RE * 8      # one flow row of a complex64 S block
+R_BLOCK_BYTES = N_ANT * B_RE * 8
+
+
+class bf_group(ctypes.Structure):
+    """One group of blocks sharing precoder `prec_id` (byte offsets)."""
+    _fields_ = [("prec_id", c_int32), ("n_blocks", c_int32), ("s_off", c_int64), ("r_off", c_int64)]
+
+
+class BfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libbf.so (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libbf.so is not built at {LIB_PATH}; run `python -m paper_1810_11451_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "bf_plan_create": (c_int, [c_int, c_int, c_int, POINTER(c_void_p)]),
+            "bf_plan_destroy": (c_int, [c_void_p]),
+            "bf_last_error": (c_char_p, [c_void_p]),
+            "bf_status_string": (c_char_p, [c_int]),
+            "bf_device_status": (c_int, [c_void_p]),
+            "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
+            "bf_held_block_bytes": (c_int64, [c_int, c_int]),
+            "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
+                                            POINTER(c_int64), c_void_p, c_void_p]),
+            "bf_apply_batch": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
+                                       c_void_p]),
+            "bf_apply_batch_host": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
+                                            c_void_p]),
+            "bf_batch_create": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
+                                        POINTER(c_void_p)]),
+            "bf_batch_launch": (c_int, [c_void_p, c_void_p]),
+            "bf_batch_destroy": (c_int, [c_void_p]),
+            "bf_errnorm": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
+            "bf_plan_launch_count": (c_int64, [c_void_p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return lib().bf_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+# ---------------------------------------------------------------- marshalling
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):  # numpy array (host memory)
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return int(torch.cuda.current_stream().cuda_stream) or None
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s or None
+    return int(s.cuda_stream) or None
+
+
+def make_groups(groups: Iterable) -> Tuple[ctypes.Array, int]:
+    """ctypes array of bf_group from (prec_id, n_blocks, s_off, r_off) tuples."""
+    gl = list(groups)
+    arr = (bf_group * max(1, len(gl)))()
+    for i, g in enumerate(gl):
+        if isinstance(g, bf_group):
+            arr[i] = g
+        else:
+            arr[i] = bf_group(int(g[0]), int(g[1]), int(g[2]), int(g[3]))
+    return arr, len(gl)
+
+
+def _check(status: int, plan=None):
+    if status != BF_OK:
+        raise BfError(status, bf_last_error(plan))
+
+
+# ---------------------------------------------------------------- C ABI, same names
+def bf_plan_create(n_ant: int = N_ANT, f_max: int = F_LIMIT, b: int = B_RE) -> int:
+    h = c_void_p()
+    _check(lib().bf_plan_create(n_ant, f_max, b, ctypes.byref(h)))
+    return h.value
+
+
+def bf_plan_destroy(plan) -> None:
+    _check(lib().bf_plan_destroy(plan))
+
+
+def bf_last_error(plan=None) -> str:
+    return (lib().bf_last_error(plan) or b"").decode()
+
+
+def bf_status_string(s: int) -> str:
+    return lib().bf_status_string(int(s)).decode()
+
+
+def bf_device_status(plan) -> int:
+    """BF_OK, or BF_ETIMEOUT if a kernel gave up on a bounded wait (cleared)."""
+    return int(lib().bf_device_status(plan))
+
+
+def bf_set_precoders(plan, W_dev, f_list: Sequence[int], first_id: int = 0, stream=None) -> None:
+    fa = (c_int32 * max(1, len(f_list)))(*[int(f) for f in f_list])
+    _check(lib().bf_set_precoders(plan, _ptr(W_dev), fa, len(f_list), first_id, _stream(stream)), plan)
+
+
+def bf_held_block_bytes(f: int, prec: int) -> int:
+    return int(lib().bf_held_block_bytes(int(f), int(prec)))
+
+
+def bf_quantize_symbols(plan, S_dev, groups, prec: int, Sq_dev, q_off: Sequence[int], scale_dev,
+                        stream=None) -> None:
+    ga, n = make_groups(groups)
+    qa = (c_int64 * max(1, len(q_off)))(*[int(q) for q in q_off])
+    _check(lib().bf_quantize_symbols(plan, _ptr(S_dev), ga, n, int(prec), _ptr(Sq_dev), qa, _ptr(scale_dev),
+                                     _stream(stream)), plan)
+
+
+def bf_apply_batch(plan, S_dev, scale_dev, groups, prec: int, R_dev, stream=None) -> None:
+    ga, n = make_groups(groups)
+    _check(lib().bf_apply_batch(plan, _ptr(S_dev), _ptr(scale_dev), ga, n, int(prec), _ptr(R_dev),
+                                _stream(stream)), plan)
+
+
+def bf_apply_batch_host(plan, S_host, groups, prec: int, R_host, stream=None) -> None:
+    ga, n = make_groups(groups)
+    _check(lib().bf_apply_batch_host(plan, _ptr(S_host), ga, n, int(prec), _ptr(R_host), _stream(stream)), plan)
+
+
+def bf_batch_create(plan, S_dev, scale_dev, groups, prec: int, R_dev) -> int:
+    ga, n = make_groups(groups)
+    h = c_void_p()
+    _check(lib().bf_batch_create(plan, _ptr(S_dev), _ptr(scale_dev), ga, n, int(prec), _ptr(R_dev),
+                                 ctypes.byref(h)), plan)
+    return h.value
+
+
+def bf_batch_launch(batch, stream=None) -> None:
+    st = lib().bf_batch_launch(batch, _stream(stream))
+    if st != BF_OK:
+        raise BfError(st, "bf_batch_launch failed")
+
+
+def bf_batch_destroy(batch) -> None:
+    lib().bf_batch_destroy(batch)
+
+
+def bf_errnorm(plan, R_dev, Rref_dev, n_blocks: int, per_block_dev=None, stream=None) -> Tuple[float, float]:
+    """(sum |R - Rref|^2, sum |Rref|^2) over n_blocks blocks, in FP64."""
+    tot = (c_double * 2)()
+    _check(lib().bf_errnorm(plan, _ptr(R_dev), _ptr(Rref_dev), int(n_blocks), _ptr(per_block_dev), tot,
+                            _stream(stream)), plan)
+    return float(tot[0]), float(tot[1])
+
+
+def bf_plan_launch_count(plan) -> int:
+    return int(lib().bf_plan_launch_count(plan))
+
+
+class bf_tile(ctypes.Structure):
+    """One scheduled work item (see bf_schedule in bf.h)."""
+    _fields_ = [("s_off", c_int64), ("r_off", c_int64), ("prec_id", c_int32), ("first_block", c_int32),
+                ("f", ctypes.c_int16), ("n_blocks", ctypes.c_int16), ("flags", c_int32)]
+
+
+def bf_schedule(f_of_slot: Sequence[int], groups, prec: int, held: bool, max_cta: int):
+    """The host scheduler: returns (list of bf_tile, cta_begin list)."""
+    L = lib()
+    L.bf_schedule.restype = c_int32
+    fa = (c_int32 * max(1, len(f_of_slot)))(*[int(f) for f in f_of_slot])
+    ga, n = make_groups(groups)
+    ncta = c_int32()
+    nt = L.bf_schedule(fa, len(f_of_slot), ga, n, int(prec), int(bool(held)), int(max_cta), None, 0, None,
+                       ctypes.byref(ncta))
+    if nt < 0:
+        raise BfError(-nt, "bf_schedule rejected its arguments")
+    tiles = (bf_tile * max(1, nt))()
+    begin = (c_int32 * (int(max_cta) + 1))()
+    nt = L.bf_schedule(fa, len(f_of_slot), ga, n, int(prec), int(bool(held)), int(max_cta), tiles, nt, begin,
+                       ctypes.byref(ncta))
+    if nt < 0:
+        raise BfError(-nt, "bf_schedule rejected its arguments")
+    return list(tiles)[:nt], list(begin)[:ncta.value + 1]

@@ -1,0 +1,71 @@
+// bf_internal.h -- shapes, the work-list tile and kernel parameters shared by
+// the host side of libbf and its kernels.
+#pragma once
+#include <cstdint>
+
+#include "bf.h"
+
+namespace bfi {
+
+constexpr int N_ANT = 64;    // antennas: rows of W and of R (Sec. II)
+constexpr int B_RE = 60;     // resource elements: columns of S and R (Sec. III)
+constexpr int F_LIMIT = 36;  // largest number of flows (Sec. III)
+
+constexpr int S_BYTES_PER_F = B_RE * 8;          // one flow row of S, complex64: 480 B
+constexpr int R_BLOCK_BYTES = N_ANT * B_RE * 8;  // one R block, complex64: 30,720 B
+
+// Tensor-core operands: K = 2f real columns rounded up to the MMA's K step.
+__host__ __device__ constexpr int kpad_of(int f) { return ((2 * f + 15) / 16) * 16; }
+constexpr int KPAD_MAX = kpad_of(F_LIMIT);  // 80
+
+// Bytes of one term of a 128-row bf16/fp16 operand image (a precoder image,
+// or the two-block symbol operand of one tile).
+__host__ __device__ constexpr int tc_img_bytes(int kpad) { return 128 * kpad * 2; }
+constexpr int TC_IMG_MAX = tc_img_bytes(KPAD_MAX);  // 20,480
+
+// Held S block: 64 rows x kpad columns of 16-bit values per term.
+__host__ __device__ constexpr int64_t held_block_bytes(int f, int terms) {
+    return (int64_t)terms * 64 * kpad_of(f) * 2;
+}
+
+// FP32 precoder image for the CUDA-core kernel: planar, flow-major,
+// Re W[i][k] at float index k*64 + i, Im W[i][k] at f*64 + k*64 + i.
+__host__ __device__ constexpr int simt_img_bytes(int f) { return 2 * N_ANT * f * 4; }
+constexpr int SIMT_IMG_MAX = simt_img_bytes(F_LIMIT);  // 18,432
+
+// Per-slot strides of the precoder store.
+constexpr int64_t W_SIMT_STRIDE = SIMT_IMG_MAX;
+constexpr int64_t W_BF16X2_STRIDE = 2 * TC_IMG_MAX;  // hi image then lo image, compact
+constexpr int64_t W_FP16_STRIDE = TC_IMG_MAX;
+
+// One work item: up to two consecutive blocks of one group (same precoder).
+struct Tile {
+    int64_t s_off;  // byte offset of the first block in the S buffer
+    int64_t r_off;  // byte offset of the first block in the R buffer
+    int32_t prec;   // precoder slot
+    int32_t sblk;   // index of the first block in group order (held-S scale index)
+    int16_t f;      // flows
+    int16_t nblk;   // 1 or 2
+    int32_t flags;  // TF_* bits, set by the host scheduler
+};
+
+// Tile flags, within one CTA's run of tiles and counting only tiles with f > 0.
+constexpr int TF_FIRST_OF_W = 1;  // first tile that uses its precoder
+constexpr int TF_LAST_OF_W = 2;   // last tile that uses its precoder
+static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
+
+// Kernel arguments (all pointers are device pointers).
+struct KParams {
+    const Tile *tiles;
+    const int32_t *cta_begin;  // n_cta + 1 entries: CTA c runs tiles [cta_begin[c], cta_begin[c+1])
+    const uint8_t *S;
+    uint8_t *R;
+    const float *s_scale;      // per block (held S), else nullptr
+    const uint8_t *w_simt;     // FP32 planar images, stride W_SIMT_STRIDE
+    const uint8_t *w_tc;       // bf16 hi|lo or fp16 images
+    int64_t w_tc_stride;
+    const float *w_scale;      // per slot: power of two undoing the image scale
+    int *status;               // device status word
+};
+
+}  // namespace bfi

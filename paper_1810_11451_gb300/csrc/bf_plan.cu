@@ -1,0 +1,729 @@
+// bf_plan.cu -- host side of libbf: plans, the precoder store, the work-list
+// scheduler, launches, prepared (graph-captured) batches, the host-buffer
+// pipeline and the accuracy report. The C ABI is declared in include/bf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bf_internal.h"
+#include "bf_plan.h"
+#include "bf_prep.h"
+
+using namespace bfi;
+
+static thread_local std::string g_err;  // errors with no plan (creation)
+
+bf_status bf_fail(bf_plan plan, bf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (plan) plan->err = buf;
+    else g_err = buf;
+    return s;
+}
+
+#define BF_CK(plan, call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return bf_fail((plan), BF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ small helpers
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+bf_status plan_ensure_device(bf_plan plan) {
+    int cur = -1;
+    BF_CK(plan, cudaGetDevice(&cur));
+    if (cur != plan->device) BF_CK(plan, cudaSetDevice(plan->device));
+    return BF_OK;
+}
+
+template <typename T>
+static bf_status grow_dev(bf_plan plan, T **p, size_t *cap, size_t need) {
+    if (need <= *cap) return BF_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*p) {
+        BF_CK(plan, cudaDeviceSynchronize());
+        BF_CK(plan, cudaFree(*p));
+        *p = nullptr;
+        *cap = 0;
+    }
+    if (cudaMalloc((void **)p, n) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return bf_fail(plan, BF_ENOMEM, "cudaMalloc of %zu bytes failed", n);
+    }
+    *cap = n;
+    return BF_OK;
+}
+
+static bf_status grow_pinned(bf_plan plan, uint8_t **p, size_t *cap, size_t need) {
+    if (need <= *cap) return BF_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*p) {
+        BF_CK(plan, cudaFreeHost(*p));
+        *p = nullptr;
+        *cap = 0;
+    }
+    if (cudaMallocHost((void **)p, n) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return bf_fail(plan, BF_ENOMEM, "cudaMallocHost of %zu bytes failed", n);
+    }
+    *cap = n;
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ C ABI: plan
+extern "C" const char *bf_status_string(bf_status s) {
+    switch (s) {
+        case BF_OK: return "BF_OK";
+        case BF_EINVAL: return "BF_EINVAL";
+        case BF_ENOMEM: return "BF_ENOMEM";
+        case BF_EBUDGET: return "BF_EBUDGET";
+        case BF_ECUDA: return "BF_ECUDA";
+        case BF_ETIMEOUT: return "BF_ETIMEOUT";
+        case BF_EAGAIN: return "BF_EAGAIN";
+        case BF_EBUSY: return "BF_EBUSY";
+        case BF_ENOTREADY: return "BF_ENOTREADY";
+        case BF_ENOTFOUND: return "BF_ENOTFOUND";
+    }
+    return "BF_UNKNOWN";
+}
+
+extern "C" const char *bf_last_error(bf_plan plan) { return plan ? plan->err.c_str() : g_err.c_str(); }
+
+extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
+    if (!out) return bf_fail(nullptr, BF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_ant != N_ANT) return bf_fail(nullptr, BF_EINVAL, "n_ant must be %d, got %d", N_ANT, n_ant);
+    if (b != B_RE) return bf_fail(nullptr, BF_EINVAL, "b must be %d, got %d", B_RE, b);
+    if (f_max < 0 || f_max > F_LIMIT)
+        return bf_fail(nullptr, BF_EINVAL, "f_max must be in [0, %d], got %d", F_LIMIT, f_max);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    if (prop.major != 10 || prop.minor != 3)
+        return bf_fail(nullptr, BF_ECUDA, "libbf is built for sm_103a; device %d is sm_%d%d", dev, prop.major,
+                       prop.minor);
+    static bool configured = false;
+    if (!configured) {
+        if ((e = configure_simt()) != cudaSuccess || (e = configure_tc()) != cudaSuccess)
+            return bf_fail(nullptr, BF_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
+        configured = true;
+    }
+    bf_plan p = new bf_plan_s();
+    p->device = dev;
+    p->sm_count = prop.multiProcessorCount;
+    p->n_ant = n_ant;
+    p->f_max = f_max;
+    p->b = b;
+    if (cudaMalloc((void **)&p->d_status, 64) != cudaSuccess || cudaMemset(p->d_status, 0, 64) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return bf_fail(nullptr, BF_ENOMEM, "status word allocation failed");
+    }
+    for (auto &w : p->ring) {
+        if (cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) != cudaSuccess) {
+            bf_plan_destroy(p);
+            return bf_fail(nullptr, BF_ECUDA, "cudaEventCreate failed");
+        }
+    }
+    if (cudaEventCreateWithFlags(&p->prep_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->xfer[0], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->xfer[1], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->xfer_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->xfer_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->xfer_ev[2], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        bf_plan_destroy(p);
+        return bf_fail(nullptr, BF_ECUDA, "stream/event creation failed");
+    }
+    *out = p;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_plan_destroy(bf_plan plan) {
+    if (!plan) return BF_OK;
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    for (auto &w : plan->ring) {
+        if (w.d) cudaFree(w.d);
+        if (w.h) cudaFreeHost(w.h);
+        if (w.ev) cudaEventDestroy(w.ev);
+    }
+    void *dev_ptrs[] = {plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_scale, plan->d_status,
+                        plan->prep_d, plan->en_d, plan->x_s[0], plan->x_s[1], plan->x_r[0], plan->x_r[1]};
+    for (void *q : dev_ptrs)
+        if (q) cudaFree(q);
+    if (plan->prep_h) cudaFreeHost(plan->prep_h);
+    if (plan->en_h) cudaFreeHost(plan->en_h);
+    if (plan->prep_ev) cudaEventDestroy(plan->prep_ev);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    for (int i = 0; i < 2; ++i)
+        if (plan->xfer[i]) cudaStreamDestroy(plan->xfer[i]);
+    for (int i = 0; i < 3; ++i)
+        if (plan->xfer_ev[i]) cudaEventDestroy(plan->xfer_ev[i]);
+    cudaGetLastError();
+    delete plan;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_device_status(bf_plan plan) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    BF_CK(plan, cudaDeviceSynchronize());
+    int v = 0;
+    BF_CK(plan, cudaMemcpy(&v, plan->d_status, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+        BF_CK(plan, cudaMemset(plan->d_status, 0, sizeof v));
+        return bf_fail(plan, BF_ETIMEOUT, "a kernel gave up on a bounded wait (status 0x%x)", v);
+    }
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ precoders
+static bf_status ensure_slots(bf_plan plan, int need) {
+    if (need <= plan->cap) return BF_OK;
+    int ncap = std::max(need, std::max(64, plan->cap * 2));
+    uint8_t *ns = nullptr, *nb = nullptr, *nf = nullptr;
+    float *nsc = nullptr;
+    const size_t bs = (size_t)ncap * W_SIMT_STRIDE, bb = (size_t)ncap * W_BF16X2_STRIDE,
+                 bf = (size_t)ncap * W_FP16_STRIDE, bsc = (size_t)ncap * sizeof(float);
+    if (cudaMalloc((void **)&ns, bs) != cudaSuccess || cudaMalloc((void **)&nb, bb) != cudaSuccess ||
+        cudaMalloc((void **)&nf, bf) != cudaSuccess || cudaMalloc((void **)&nsc, bsc) != cudaSuccess) {
+        cudaGetLastError();
+        if (ns) cudaFree(ns);
+        if (nb) cudaFree(nb);
+        if (nf) cudaFree(nf);
+        if (nsc) cudaFree(nsc);
+        return bf_fail(plan, BF_ENOMEM, "precoder store growth to %d slots failed", ncap);
+    }
+    BF_CK(plan, cudaDeviceSynchronize());
+    if (plan->cap) {
+        BF_CK(plan, cudaMemcpy(ns, plan->w_simt, (size_t)plan->cap * W_SIMT_STRIDE, cudaMemcpyDeviceToDevice));
+        BF_CK(plan, cudaMemcpy(nb, plan->w_bf16x2, (size_t)plan->cap * W_BF16X2_STRIDE, cudaMemcpyDeviceToDevice));
+        BF_CK(plan, cudaMemcpy(nf, plan->w_fp16, (size_t)plan->cap * W_FP16_STRIDE, cudaMemcpyDeviceToDevice));
+        BF_CK(plan, cudaMemcpy(nsc, plan->w_scale, (size_t)plan->cap * sizeof(float), cudaMemcpyDeviceToDevice));
+        cudaFree(plan->w_simt);
+        cudaFree(plan->w_bf16x2);
+        cudaFree(plan->w_fp16);
+        cudaFree(plan->w_scale);
+    }
+    plan->w_simt = ns;
+    plan->w_bf16x2 = nb;
+    plan->w_fp16 = nf;
+    plan->w_scale = nsc;
+    plan->f_slot.resize(ncap, -1);
+    plan->cap = ncap;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_host, int32_t n_prec,
+                                      int32_t first_id, void *stream) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (n_prec < 0 || first_id < 0) return bf_fail(plan, BF_EINVAL, "negative n_prec or first_id");
+    if (n_prec == 0) return BF_OK;
+    if (!W_dev || !f_host) return bf_fail(plan, BF_EINVAL, "W_dev or f_host is NULL");
+    if (((uintptr_t)W_dev & 7u) != 0) return bf_fail(plan, BF_EINVAL, "W_dev must be 8-byte aligned");
+    if ((int64_t)first_id + n_prec > (1 << 24)) return bf_fail(plan, BF_EINVAL, "slot id too large");
+    for (int i = 0; i < n_prec; ++i)
+        if (f_host[i] < 0 || f_host[i] > plan->f_max)
+            return bf_fail(plan, BF_EINVAL, "precoder %d: f = %d outside [0, f_max = %d]", i, f_host[i],
+                           plan->f_max);
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    if ((s = ensure_slots(plan, first_id + n_prec)) != BF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n_prec * sizeof(PrecJob);
+    // The staging buffers may still be read by the previous conversion.
+    BF_CK(plan, cudaEventSynchronize(plan->prep_ev));
+    if ((s = grow_pinned(plan, &plan->prep_h, &plan->prep_hcap, bytes)) != BF_OK) return s;
+    if ((s = grow_dev(plan, &plan->prep_d, &plan->prep_cap, bytes)) != BF_OK) return s;
+    PrecJob *jobs = reinterpret_cast<PrecJob *>(plan->prep_h);
+    int64_t off = 0;
+    for (int i = 0; i < n_prec; ++i) {
+        jobs[i].w_off = off;
+        jobs[i].f = f_host[i];
+        jobs[i].slot = first_id + i;
+        off += (int64_t)N_ANT * f_host[i];
+    }
+    BF_CK(plan, cudaMemcpyAsync(plan->prep_d, plan->prep_h, bytes, cudaMemcpyHostToDevice, st));
+    BF_CK(plan, launch_precoders(reinterpret_cast<const float2 *>(W_dev), reinterpret_cast<PrecJob *>(plan->prep_d),
+                                 n_prec, plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_scale, st));
+    BF_CK(plan, cudaEventRecord(plan->prep_ev, st));
+    for (int i = 0; i < n_prec; ++i) plan->f_slot[first_id + i] = f_host[i];
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ held symbols
+extern "C" int64_t bf_held_block_bytes(int f, bf_precision prec) {
+    if (f < 0 || f > F_LIMIT) return 0;
+    if (prec == BF_BF16 || prec == BF_FP16) return held_block_bytes(f, 1);
+    if (prec == BF_BF16X3) return held_block_bytes(f, 2);
+    return 0;
+}
+
+static bf_status check_group_slots(bf_plan plan, const bf_group *groups, int32_t n_groups) {
+    for (int g = 0; g < n_groups; ++g) {
+        const bf_group &gr = groups[g];
+        if (gr.n_blocks < 0) return bf_fail(plan, BF_EINVAL, "group %d: negative n_blocks", g);
+        if (gr.prec_id < 0 || gr.prec_id >= plan->cap || plan->f_slot[gr.prec_id] < 0)
+            return bf_fail(plan, BF_ENOTFOUND, "group %d: precoder slot %d is not set", g, gr.prec_id);
+        if (gr.s_off < 0 || gr.r_off < 0 || (gr.s_off & 15) || (gr.r_off & 15))
+            return bf_fail(plan, BF_EINVAL, "group %d: offsets must be non-negative multiples of 16", g);
+    }
+    return BF_OK;
+}
+
+extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const bf_group *groups, int32_t n_groups,
+                                         bf_precision prec, void *Sq_dev, const int64_t *q_off_host,
+                                         float *scale_dev, void *stream) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (n_groups < 0) return bf_fail(plan, BF_EINVAL, "negative n_groups");
+    if (prec != BF_BF16 && prec != BF_FP16 && prec != BF_BF16X3)
+        return bf_fail(plan, BF_EINVAL, "held S exists for BF_BF16, BF_FP16 and BF_BF16X3 only");
+    if (n_groups == 0) return BF_OK;
+    if (!groups || !q_off_host || !S_dev || !Sq_dev || !scale_dev)
+        return bf_fail(plan, BF_EINVAL, "NULL argument");
+    if (!aligned16(S_dev) || !aligned16(Sq_dev) || ((uintptr_t)scale_dev & 3u))
+        return bf_fail(plan, BF_EINVAL, "S_dev and Sq_dev must be 16-byte aligned");
+    bf_status s = check_group_slots(plan, groups, n_groups);
+    if (s != BF_OK) return s;
+    for (int g = 0; g < n_groups; ++g)
+        if (q_off_host[g] < 0 || (q_off_host[g] & 15))
+            return bf_fail(plan, BF_EINVAL, "group %d: q_off must be a non-negative multiple of 16", g);
+    if ((s = plan_ensure_device(plan)) != BF_OK) return s;
+    BF_CK(plan, cudaEventSynchronize(plan->prep_ev));
+    const size_t bytes = (size_t)n_groups * sizeof(QGroup);
+    if ((s = grow_pinned(plan, &plan->prep_h, &plan->prep_hcap, bytes)) != BF_OK) return s;
+    if ((s = grow_dev(plan, &plan->prep_d, &plan->prep_cap, bytes)) != BF_OK) return s;
+    QGroup *q = reinterpret_cast<QGroup *>(plan->prep_h);
+    int blk = 0, max_nb = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        q[g].s_off = groups[g].s_off;
+        q[g].q_off = q_off_host[g];
+        q[g].f = plan->f_slot[groups[g].prec_id];
+        q[g].nb = groups[g].n_blocks;
+        q[g].blk0 = blk;
+        q[g].pad = 0;
+        blk += groups[g].n_blocks;
+        max_nb = std::max(max_nb, (int)groups[g].n_blocks);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    BF_CK(plan, cudaMemcpyAsync(plan->prep_d, plan->prep_h, bytes, cudaMemcpyHostToDevice, st));
+    BF_CK(plan, launch_quantize(prec, (const uint8_t *)S_dev, reinterpret_cast<QGroup *>(plan->prep_d), n_groups,
+                                max_nb, (uint8_t *)Sq_dev, scale_dev, st));
+    BF_CK(plan, cudaEventRecord(plan->prep_ev, st));
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ work lists
+// Tiles of up to `tile_blocks` consecutive blocks of one group; the run of
+// tiles is split into n_cta contiguous ranges of about equal cost (bytes
+// moved, weighted per f by the autotune table), so each CTA loads a precoder
+// once per range and streams its S blocks.
+void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *groups, int32_t n_groups,
+                    bf_precision prec, bool held, int max_cta, WorkList &wl) {
+    wl.tiles.clear();
+    wl.cta_begin.clear();
+    const int tile_blocks = 2;
+    std::vector<double> cost;
+    int blk = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        const bf_group &gr = groups[g];
+        const int f = f_slot[gr.prec_id];
+        const int64_t sb = held ? bf_held_block_bytes(f, prec) : (int64_t)f * S_BYTES_PER_F;
+        const double w = tune.cost_weight(prec, f);
+        for (int b0 = 0; b0 < gr.n_blocks; b0 += tile_blocks) {
+            Tile t{};
+            t.s_off = gr.s_off + (int64_t)b0 * sb;
+            t.r_off = gr.r_off + (int64_t)b0 * R_BLOCK_BYTES;
+            t.prec = gr.prec_id;
+            t.sblk = blk + b0;
+            t.f = (int16_t)f;
+            t.nblk = (int16_t)std::min(tile_blocks, gr.n_blocks - b0);
+            t.flags = 0;
+            wl.tiles.push_back(t);
+            cost.push_back(w * t.nblk * (double)(sb + R_BLOCK_BYTES));
+        }
+        blk += gr.n_blocks;
+    }
+    const int n_tiles = (int)wl.tiles.size();
+    const int n_cta = std::max(1, std::min(max_cta, n_tiles));
+    double total = 0;
+    for (double c : cost) total += c;
+    wl.cta_begin.assign(n_cta + 1, n_tiles);
+    wl.cta_begin[0] = 0;
+    // midpoint rule: tile t goes to CTA floor((cum + cost/2) / (total / n_cta)),
+    // clamped so that ranges stay contiguous and no CTA is left empty
+    double cum = 0;
+    int cur = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        int c = total > 0 ? (int)((cum + 0.5 * cost[t]) * n_cta / total) : 0;
+        const int lo = std::max(cur, n_cta - (n_tiles - t));
+        const int hi = std::min(t > 0 ? cur + 1 : 0, n_cta - 1);
+        c = std::min(std::max(c, lo), hi);
+        while (cur < c) wl.cta_begin[++cur] = t;
+        cum += cost[t];
+    }
+    while (cur < n_cta) wl.cta_begin[++cur] = n_tiles;
+    // precoder-run flags within each CTA's range (tiles with f > 0 only)
+    for (int c = 0; c < n_cta; ++c) {
+        int prev = -1;
+        int last_idx = -1;
+        for (int t = wl.cta_begin[c]; t < wl.cta_begin[c + 1]; ++t) {
+            Tile &tl = wl.tiles[t];
+            if (tl.f == 0) continue;
+            if (tl.prec != prev) {
+                tl.flags |= TF_FIRST_OF_W;
+                if (last_idx >= 0) wl.tiles[last_idx].flags |= TF_LAST_OF_W;
+            }
+            prev = tl.prec;
+            last_idx = t;
+        }
+        if (last_idx >= 0) wl.tiles[last_idx].flags |= TF_LAST_OF_W;
+    }
+}
+
+extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *groups, int32_t n_groups,
+                               bf_precision prec, int32_t held, int32_t max_cta, bf_tile *tiles_out,
+                               int32_t max_tiles, int32_t *cta_begin_out, int32_t *n_cta_out) {
+    if (!f_of_slot || n_slots < 0 || n_groups < 0 || (n_groups && !groups) || max_cta < 1 || !n_cta_out ||
+        prec < BF_FP32 || prec > BF_BF16X3 || (held && prec == BF_FP32))
+        return -BF_EINVAL;
+    for (int g = 0; g < n_groups; ++g) {
+        if (groups[g].prec_id < 0 || groups[g].prec_id >= n_slots || groups[g].n_blocks < 0) return -BF_EINVAL;
+        const int f = f_of_slot[groups[g].prec_id];
+        if (f < 0 || f > F_LIMIT) return -BF_EINVAL;
+    }
+    WorkList wl;
+    TuneTable tune;
+    build_worklist(f_of_slot, tune, groups, n_groups, prec, held != 0, max_cta, wl);
+    const int nt = (int)wl.tiles.size();
+    *n_cta_out = (int32_t)wl.cta_begin.size() - 1;
+    if (!tiles_out) return nt;  // size query
+    if (nt > max_tiles || !cta_begin_out) return -BF_EINVAL;
+    for (int t = 0; t < nt; ++t) {
+        const Tile &a = wl.tiles[t];
+        bf_tile &o = tiles_out[t];
+        o.s_off = a.s_off;
+        o.r_off = a.r_off;
+        o.prec_id = a.prec;
+        o.first_block = a.sblk;
+        o.f = a.f;
+        o.n_blocks = a.nblk;
+        o.flags = a.flags;
+    }
+    for (size_t c = 0; c < wl.cta_begin.size(); ++c) cta_begin_out[c] = wl.cta_begin[c];
+    return nt;
+}
+
+static bf_status validate_apply(bf_plan plan, const void *S, const float *scale, const bf_group *groups,
+                                int32_t n_groups, bf_precision prec, const void *R, bool device_ptrs) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (n_groups < 0) return bf_fail(plan, BF_EINVAL, "negative n_groups");
+    if (prec < BF_FP32 || prec > BF_BF16X3) return bf_fail(plan, BF_EINVAL, "unknown precision %d", (int)prec);
+    if (scale && prec == BF_FP32) return bf_fail(plan, BF_EINVAL, "BF_FP32 takes complex64 S (scale_dev must be NULL)");
+    if (n_groups == 0) return BF_OK;
+    if (!groups || !S || !R) return bf_fail(plan, BF_EINVAL, "NULL argument");
+    if (device_ptrs && (!aligned16(S) || !aligned16(R)))
+        return bf_fail(plan, BF_EINVAL, "S_dev and R_dev must be 16-byte aligned");
+    if (scale && ((uintptr_t)scale & 3u)) return bf_fail(plan, BF_EINVAL, "scale_dev must be 4-byte aligned");
+    return check_group_slots(plan, groups, n_groups);
+}
+
+static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_bytes, const void *S, const float *scale,
+                           void *R, bf_precision prec) {
+    KParams p{};
+    p.tiles = reinterpret_cast<const Tile *>(dlist);
+    p.cta_begin = reinterpret_cast<const int32_t *>(dlist + tiles_bytes);
+    p.S = (const uint8_t *)S;
+    p.R = (uint8_t *)R;
+    p.s_scale = scale;
+    p.w_simt = plan->w_simt;
+    p.w_tc = prec == BF_FP16 ? plan->w_fp16 : plan->w_bf16x2;
+    p.w_tc_stride = prec == BF_FP16 ? W_FP16_STRIDE : W_BF16X2_STRIDE;
+    p.w_scale = plan->w_scale;
+    p.status = plan->d_status;
+    return p;
+}
+
+int max_cta_for(bf_plan plan, bf_precision prec) {
+    const int per_sm = prec == BF_FP32 ? plan->tune.simt_ctas_per_sm : 1;
+    return plan->sm_count * per_sm;
+}
+
+cudaError_t launch_kernel(bf_precision prec, bool held, const KParams &p, int n_cta, cudaStream_t st) {
+    if (prec == BF_FP32) return launch_simt(p, n_cta, st);
+    return launch_tc((int)prec, held, p, n_cta, st);
+}
+
+// Upload a work list through the plan's ring (one entry per call in flight)
+// and launch it. `max_cta` <= 0 means the tuned default.
+bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const bf_group *groups, int32_t n_groups,
+                        bf_precision prec, void *R, cudaStream_t st, int max_cta) {
+    const bool held = scale != nullptr;
+    WorkList &wl = plan->scratch_wl;
+    build_worklist(plan->f_slot.data(), plan->tune, groups, n_groups, prec, held,
+                   max_cta > 0 ? max_cta : max_cta_for(plan, prec), wl);
+    if (wl.tiles.empty()) return BF_OK;
+    bf_status s;
+    const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
+    const size_t bytes = tb + cb;
+    // reuse an entry that already holds exactly this list
+    WorkBuf *hit = nullptr;
+    for (auto &w : plan->ring)
+        if (w.valid && w.bytes == bytes && w.tiles_bytes == tb &&
+            std::memcmp(w.h, wl.tiles.data(), tb) == 0 && std::memcmp(w.h + tb, wl.cta_begin.data(), cb) == 0) {
+            hit = &w;
+            break;
+        }
+    if (!hit) {
+        WorkBuf &w = plan->ring[plan->ring_next];
+        plan->ring_next = (plan->ring_next + 1) % (int)(sizeof(plan->ring) / sizeof(plan->ring[0]));
+        BF_CK(plan, cudaEventSynchronize(w.ev));  // its previous launch has finished reading it
+        w.valid = false;
+        if ((s = grow_pinned(plan, &w.h, &w.hcap, bytes)) != BF_OK) return s;
+        if ((s = grow_dev(plan, &w.d, &w.cap, bytes)) != BF_OK) return s;
+        std::memcpy(w.h, wl.tiles.data(), tb);
+        std::memcpy(w.h + tb, wl.cta_begin.data(), cb);
+        BF_CK(plan, cudaMemcpyAsync(w.d, w.h, bytes, cudaMemcpyHostToDevice, st));
+        w.bytes = bytes;
+        w.tiles_bytes = tb;
+        w.valid = true;
+        hit = &w;
+    } else {
+        // the cached device copy may be in use on another stream: order after it
+        BF_CK(plan, cudaStreamWaitEvent(st, hit->ev, 0));
+    }
+    const KParams p = make_params(plan, hit->d, tb, S, scale, R, prec);
+    BF_CK(plan, launch_kernel(prec, held, p, (int)wl.cta_begin.size() - 1, st));
+    BF_CK(plan, cudaEventRecord(hit->ev, st));
+    plan->launches++;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_apply_batch(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
+                                    int32_t n_groups, bf_precision prec, void *R_dev, void *stream) {
+    bf_status s = validate_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, true);
+    if (s != BF_OK || n_groups == 0) return s;
+    if ((s = plan_ensure_device(plan)) != BF_OK) return s;
+    return enqueue_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, (cudaStream_t)stream, 0);
+}
+
+// ------------------------------------------------------------------ prepared batches
+struct bf_batch_s {
+    bf_plan plan = nullptr;
+    uint8_t *d = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
+                                     int32_t n_groups, bf_precision prec, void *R_dev, bf_batch *out) {
+    if (!out) return bf_fail(plan, BF_EINVAL, "out is NULL");
+    *out = nullptr;
+    bf_status s = validate_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, true);
+    if (s != BF_OK) return s;
+    if ((s = plan_ensure_device(plan)) != BF_OK) return s;
+    WorkList wl;
+    build_worklist(plan->f_slot.data(), plan->tune, groups, n_groups, prec, scale_dev != nullptr,
+                   max_cta_for(plan, prec), wl);
+    bf_batch bt = new bf_batch_s();
+    bt->plan = plan;
+    const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
+    if (!wl.tiles.empty()) {
+        if (cudaMalloc((void **)&bt->d, tb + cb) != cudaSuccess) {
+            cudaGetLastError();
+            delete bt;
+            return bf_fail(plan, BF_ENOMEM, "work-list allocation failed");
+        }
+        cudaError_t e = cudaMemcpy(bt->d, wl.tiles.data(), tb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(bt->d + tb, wl.cta_begin.data(), cb, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            bf_batch_destroy(bt);
+            return bf_fail(plan, BF_ECUDA, "work-list upload: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess && !wl.tiles.empty()) {
+        const KParams p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec);
+        cudaError_t le = launch_kernel(prec, scale_dev != nullptr, p, (int)wl.cta_begin.size() - 1, plan->cap_stream);
+        if (le != cudaSuccess) e = le;
+    }
+    cudaError_t ee = cudaStreamEndCapture(plan->cap_stream, &bt->graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bf_batch_destroy(bt);
+        return bf_fail(plan, BF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    *out = bt;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_batch_launch(bf_batch batch, void *stream) {
+    if (!batch) return bf_fail(nullptr, BF_EINVAL, "batch is NULL");
+    bf_plan plan = batch->plan;
+    BF_CK(plan, cudaGraphLaunch(batch->exec, (cudaStream_t)stream));
+    plan->launches++;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_batch_destroy(bf_batch batch) {
+    if (!batch) return BF_OK;
+    cudaSetDevice(batch->plan->device);
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    if (batch->graph) cudaGraphDestroy(batch->graph);
+    if (batch->d) {
+        cudaDeviceSynchronize();
+        cudaFree(batch->d);
+    }
+    cudaGetLastError();
+    delete batch;
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ host buffers
+// Chunks of consecutive groups are copied in, multiplied and copied out on two
+// internal streams, so the copies of one chunk overlap the kernel of another.
+extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups, int32_t n_groups,
+                                         bf_precision prec, void *R_host, void *stream) {
+    bf_status s = validate_apply(plan, S_host, nullptr, groups, n_groups, prec, R_host, false);
+    if (s != BF_OK || n_groups == 0) return s;
+    if ((s = plan_ensure_device(plan)) != BF_OK) return s;
+    cudaStream_t user = (cudaStream_t)stream;
+    // chunking by bytes
+    const int64_t target = plan->host_chunk_bytes;
+    std::vector<int> cut{0};
+    int64_t acc = 0, max_s = 0, max_r = 0, cs = 0, cr = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        const int f = plan->f_slot[groups[g].prec_id];
+        const int64_t sb = (int64_t)groups[g].n_blocks * f * S_BYTES_PER_F;
+        const int64_t rb = (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
+        if (acc > 0 && acc + sb + rb > target) {
+            cut.push_back(g);
+            max_s = std::max(max_s, cs);
+            max_r = std::max(max_r, cr);
+            acc = cs = cr = 0;
+        }
+        acc += sb + rb;
+        cs += (sb + 15) & ~(int64_t)15;
+        cr += rb;
+    }
+    cut.push_back(n_groups);
+    max_s = std::max(max_s, cs);
+    max_r = std::max(max_r, cr);
+    for (int i = 0; i < 2; ++i) {
+        if ((s = grow_dev(plan, &plan->x_s[i], &plan->x_scap[i], (size_t)std::max<int64_t>(max_s, 16))) != BF_OK) return s;
+        if ((s = grow_dev(plan, &plan->x_r[i], &plan->x_rcap[i], (size_t)std::max<int64_t>(max_r, 16))) != BF_OK) return s;
+    }
+    BF_CK(plan, cudaEventRecord(plan->xfer_ev[2], user));
+    BF_CK(plan, cudaStreamWaitEvent(plan->xfer[0], plan->xfer_ev[2], 0));
+    BF_CK(plan, cudaStreamWaitEvent(plan->xfer[1], plan->xfer_ev[2], 0));
+    std::vector<bf_group> local;
+    for (size_t c = 0; c + 1 < cut.size(); ++c) {
+        const int i = (int)(c & 1);
+        cudaStream_t st = plan->xfer[i];
+        local.clear();
+        int64_t so = 0, ro = 0;
+        // copy S in, merging groups that are contiguous in the host buffer
+        int64_t run_src = -1, run_dst = 0, run_len = 0;
+        for (int g = cut[c]; g < cut[c + 1]; ++g) {
+            const int f = plan->f_slot[groups[g].prec_id];
+            const int64_t sb = (int64_t)groups[g].n_blocks * f * S_BYTES_PER_F;
+            bf_group lg = groups[g];
+            lg.s_off = so;
+            lg.r_off = ro;
+            local.push_back(lg);
+            if (sb > 0) {
+                if (run_src >= 0 && run_src + run_len == groups[g].s_off && run_dst + run_len == so) {
+                    run_len += sb;
+                } else {
+                    if (run_len > 0)
+                        BF_CK(plan, cudaMemcpyAsync(plan->x_s[i] + run_dst, (const uint8_t *)S_host + run_src, run_len,
+                                                    cudaMemcpyHostToDevice, st));
+                    run_src = groups[g].s_off;
+                    run_dst = so;
+                    run_len = sb;
+                }
+            }
+            so += (sb + 15) & ~(int64_t)15;
+            ro += (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
+        }
+        if (run_len > 0)
+            BF_CK(plan, cudaMemcpyAsync(plan->x_s[i] + run_dst, (const uint8_t *)S_host + run_src, run_len,
+                                        cudaMemcpyHostToDevice, st));
+        if ((s = enqueue_apply(plan, plan->x_s[i], nullptr, local.data(), (int32_t)local.size(), prec, plan->x_r[i], st,
+                               0)) != BF_OK)
+            return s;
+        // copy R out, merging contiguous destinations
+        int64_t rsrc = 0, rdst = -1, rlen = 0;
+        for (int g = cut[c]; g < cut[c + 1]; ++g) {
+            const int64_t rb = (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
+            const int64_t lo = local[g - cut[c]].r_off;
+            if (rb == 0) continue;
+            if (rdst >= 0 && rdst + rlen == groups[g].r_off && rsrc + rlen == lo) {
+                rlen += rb;
+            } else {
+                if (rlen > 0)
+                    BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[i] + rsrc, rlen,
+                                                cudaMemcpyDeviceToHost, st));
+                rsrc = lo;
+                rdst = groups[g].r_off;
+                rlen = rb;
+            }
+        }
+        if (rlen > 0)
+            BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[i] + rsrc, rlen, cudaMemcpyDeviceToHost, st));
+    }
+    BF_CK(plan, cudaEventRecord(plan->xfer_ev[0], plan->xfer[0]));
+    BF_CK(plan, cudaEventRecord(plan->xfer_ev[1], plan->xfer[1]));
+    BF_CK(plan, cudaStreamWaitEvent(user, plan->xfer_ev[0], 0));
+    BF_CK(plan, cudaStreamWaitEvent(user, plan->xfer_ev[1], 0));
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ accuracy report
+extern "C" bf_status bf_errnorm(bf_plan plan, const void *R_dev, const void *Rref_dev, int64_t n_blocks,
+                                double *per_block_dev, double *total_host, void *stream) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (n_blocks < 0 || !total_host) return bf_fail(plan, BF_EINVAL, "bad n_blocks or NULL total_host");
+    if (n_blocks > 0 && (!R_dev || !Rref_dev)) return bf_fail(plan, BF_EINVAL, "NULL R_dev or Rref_dev");
+    if ((R_dev && !aligned16(R_dev)) || (Rref_dev && !aligned16(Rref_dev)) ||
+        (per_block_dev && ((uintptr_t)per_block_dev & 7u)))
+        return bf_fail(plan, BF_EINVAL, "misaligned pointer");
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *pb = per_block_dev;
+    const size_t need = ((size_t)(per_block_dev ? 0 : 2 * n_blocks) + 2) * sizeof(double);
+    if ((s = grow_dev(plan, &plan->en_d, &plan->en_cap, need)) != BF_OK) return s;
+    if ((s = grow_pinned(plan, &plan->en_h, &plan->en_hcap, 2 * sizeof(double))) != BF_OK) return s;
+    double *total_dev = plan->en_d;
+    if (!pb) pb = plan->en_d + 2;
+    BF_CK(plan, launch_errnorm((const float2 *)R_dev, (const double2 *)Rref_dev, n_blocks, pb, total_dev,
+                               plan->sm_count * 8, st));
+    BF_CK(plan, cudaMemcpyAsync(plan->en_h, total_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BF_CK(plan, cudaStreamSynchronize(st));
+    std::memcpy(total_host, plan->en_h, 2 * sizeof(double));
+    return BF_OK;
+}
+
+extern "C" int64_t bf_plan_launch_count(bf_plan plan) { return plan ? plan->launches : 0; }

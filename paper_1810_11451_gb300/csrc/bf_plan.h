@@ -1,0 +1,92 @@
+// bf_plan.h -- the plan object behind the C ABI (host side only).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bf.h"
+#include "bf_internal.h"
+
+namespace bfi {
+
+// Autotune table: per precision and f bucket, the measured cost of one block
+// relative to its byte count (weights the static split of uneven batches),
+// and the launch shape of the CUDA-core kernel.
+constexpr int TUNE_BUCKETS = 5;  // f in [0], [1,8], [9,16], [17,24], [25,36]
+__host__ __device__ constexpr int f_bucket(int f) {
+    return f <= 0 ? 0 : (f <= 8 ? 1 : (f <= 16 ? 2 : (f <= 24 ? 3 : 4)));
+}
+
+struct TuneTable {
+    double weight[4][TUNE_BUCKETS];  // [precision][bucket], 1.0 = cost proportional to bytes
+    int simt_ctas_per_sm = 2;
+    bool tuned = false;
+    TuneTable() {
+        for (auto &row : weight)
+            for (double &w : row) w = 1.0;
+    }
+    double cost_weight(int prec, int f) const { return weight[prec & 3][f_bucket(f)]; }
+};
+
+struct WorkList {
+    std::vector<Tile> tiles;
+    std::vector<int32_t> cta_begin;
+};
+
+// One work-list buffer of the ring: pinned host image, device copy, and the
+// event recorded after the launch that reads it.
+struct WorkBuf {
+    uint8_t *d = nullptr;
+    size_t cap = 0;
+    uint8_t *h = nullptr;
+    size_t hcap = 0;
+    cudaEvent_t ev = nullptr;
+    bool valid = false;
+    size_t bytes = 0, tiles_bytes = 0;
+};
+
+}  // namespace bfi
+
+struct bf_plan_s {
+    int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
+    std::string err;
+    // precoder store (slots)
+    int cap = 0;
+    std::vector<int> f_slot;  // -1 = unset
+    uint8_t *w_simt = nullptr, *w_bf16x2 = nullptr, *w_fp16 = nullptr;
+    float *w_scale = nullptr;
+    int *d_status = nullptr;
+    // work-list ring
+    bfi::WorkBuf ring[8];
+    int ring_next = 0;
+    bfi::WorkList scratch_wl;
+    // prep staging
+    uint8_t *prep_d = nullptr, *prep_h = nullptr;
+    size_t prep_cap = 0, prep_hcap = 0;
+    cudaEvent_t prep_ev = nullptr;
+    // accuracy report
+    double *en_d = nullptr;
+    uint8_t *en_h = nullptr;
+    size_t en_cap = 0, en_hcap = 0;
+    // graph capture and host-buffer pipeline
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t xfer[2] = {nullptr, nullptr};
+    cudaEvent_t xfer_ev[3] = {nullptr, nullptr, nullptr};
+    uint8_t *x_s[2] = {nullptr, nullptr}, *x_r[2] = {nullptr, nullptr};
+    size_t x_scap[2] = {0, 0}, x_rcap[2] = {0, 0};
+    int64_t host_chunk_bytes = 24 << 20;
+    // tuning and counters
+    bfi::TuneTable tune;
+    int64_t launches = 0;
+};
+
+bf_status bf_fail(bf_plan plan, bf_status s, const char *fmt, ...);
+bf_status plan_ensure_device(bf_plan plan);
+void build_worklist(const int *f_slot, const bfi::TuneTable &tune, const bf_group *groups, int32_t n_groups,
+                    bf_precision prec, bool held, int max_cta, bfi::WorkList &wl);
+bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const bf_group *groups, int32_t n_groups,
+                        bf_precision prec, void *R, cudaStream_t st, int max_cta);
+int max_cta_for(bf_plan plan, bf_precision prec);
+cudaError_t launch_kernel(bf_precision prec, bool held, const bfi::KParams &p, int n_cta, cudaStream_t st);

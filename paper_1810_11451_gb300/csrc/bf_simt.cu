@@ -1,0 +1,196 @@
+// bf_simt.cu -- plain FP32 form of R = W x S on the CUDA cores (Sec. III,
+// beamforming equation). Each complex multiply-add is four FP32 fused
+// multiply-adds; no operand is reordered or shuffled in the inner loop (the
+// paper's three inefficiencies of the original code -- extra flops, no FMA,
+// many permutations -- do not arise).
+//
+// Persistent CTA over a cost-balanced run of tiles. One producer warp streams
+// each block of S (480*f contiguous bytes) into a shared-memory ring with bulk
+// copies and loads each precoder image once per run of tiles that share it
+// (W is constant across many S, Sec. III), double-buffered so the next W
+// arrives while the current one is in use. Eight compute warps each own 8
+// antennas (rows of R); lane l owns resource elements 2l and 2l+1 (lanes 30
+// and 31 idle). Per flow k a lane reads its two S values with one 16-byte
+// shared load and the warp's 8+8 W values as broadcasts, then issues 64 FFMA.
+// R rows are written with 16-byte stores, 480 contiguous bytes per warp.
+#include <cuda_runtime.h>
+
+#include "bf_device.cuh"
+#include "bf_internal.h"
+
+namespace bfi {
+
+constexpr int SIMT_CWARPS = 8;                         // compute warps
+constexpr int SIMT_THREADS = (SIMT_CWARPS + 1) * 32;   // + one producer warp
+constexpr int SIMT_NS = 2;                             // S ring stages
+constexpr int SIMT_NW = 2;                             // W buffers
+constexpr int SIMT_S_STAGE = F_LIMIT * S_BYTES_PER_F;  // 17,280 B
+constexpr int SIMT_OFF_S = SIMT_NW * SIMT_IMG_MAX;
+constexpr int SIMT_OFF_BAR = SIMT_OFF_S + SIMT_NS * SIMT_S_STAGE;
+constexpr int SIMT_NBARS = 2 * SIMT_NS + 2 * SIMT_NW;
+constexpr int SIMT_SMEM = SIMT_OFF_BAR + SIMT_NBARS * 8 + 16;
+
+__global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SIMT_OFF_BAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + SIMT_NBARS);
+    const uint32_t bar0 = bfd::smem_u32(bars);
+    auto s_full = [&](int s) { return bar0 + 8u * s; };
+    auto s_empty = [&](int s) { return bar0 + 8u * (SIMT_NS + s); };
+    auto w_full = [&](int w) { return bar0 + 8u * (2 * SIMT_NS + w); };
+    auto w_empty = [&](int w) { return bar0 + 8u * (2 * SIMT_NS + SIMT_NW + w); };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SIMT_NS; ++s) {
+            bfd::mbar_init(s_full(s), 1);
+            bfd::mbar_init(s_empty(s), SIMT_CWARPS);
+        }
+        for (int w = 0; w < SIMT_NW; ++w) {
+            bfd::mbar_init(w_full(w), 1);
+            bfd::mbar_init(w_empty(w), SIMT_CWARPS);
+        }
+        *abort_flag = 0;
+        bfd::mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (warp == SIMT_CWARPS) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int nS = 0, nW = 0;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const Tile tl = p.tiles[t];
+                if (tl.f == 0) continue;
+                if (tl.flags & TF_FIRST_OF_W) {
+                    const int wb = nW % SIMT_NW;
+                    if (!bfd::mbar_wait(w_empty(wb), ((nW / SIMT_NW) + 1) & 1, abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bytes = (uint32_t)simt_img_bytes(tl.f);
+                    bfd::mbar_arrive_expect_tx(w_full(wb), bytes);
+                    bfd::bulk_g2s(bfd::smem_u32(smem + wb * SIMT_IMG_MAX),
+                                  p.w_simt + (int64_t)tl.prec * W_SIMT_STRIDE, bytes, w_full(wb));
+                    ++nW;
+                }
+                const uint32_t bytes = (uint32_t)(tl.f * S_BYTES_PER_F);
+                for (int b = 0; b < tl.nblk; ++b) {
+                    const int st = nS % SIMT_NS;
+                    if (!bfd::mbar_wait(s_empty(st), ((nS / SIMT_NS) + 1) & 1, abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    bfd::mbar_arrive_expect_tx(s_full(st), bytes);
+                    bfd::bulk_g2s(bfd::smem_u32(smem + SIMT_OFF_S + st * SIMT_S_STAGE),
+                                  p.S + tl.s_off + (int64_t)b * bytes, bytes, s_full(st));
+                    ++nS;
+                }
+            }
+            // Never leave the CTA while one of its bulk copies may still be
+            // writing shared memory (only possible after an abort).
+            for (int n = nS > SIMT_NS ? nS - SIMT_NS : 0; n < nS; ++n)
+                bfd::mbar_wait_drain(s_full(n % SIMT_NS), (n / SIMT_NS) & 1, 1000000000ull);
+            for (int n = nW > SIMT_NW ? nW - SIMT_NW : 0; n < nW; ++n)
+                bfd::mbar_wait_drain(w_full(n % SIMT_NW), (n / SIMT_NW) & 1, 1000000000ull);
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const int i0 = warp * 8;            // first antenna of this warp
+        const int jl = lane < 30 ? lane : 29;  // lanes 30, 31 mirror lane 29 and store nothing
+        int nS = 0, nW = 0, wb = 0;
+        bool ok = true;
+        for (int t = t0; t < t1 && ok; ++t) {
+            const Tile tl = p.tiles[t];
+            const int f = tl.f;
+            if (f == 0) {
+                // empty sum: R = 0
+                if (lane < 30) {
+                    for (int b = 0; b < tl.nblk; ++b) {
+                        uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
+#pragma unroll
+                        for (int r = 0; r < 8; ++r)
+                            *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
+                                make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                continue;
+            }
+            if (tl.flags & TF_FIRST_OF_W) {
+                wb = nW % SIMT_NW;
+                if (!bfd::mbar_wait(w_full(wb), (nW / SIMT_NW) & 1, abort_flag, p.status)) {
+                    ok = false;
+                    break;
+                }
+                ++nW;
+            }
+            const float *Wr = reinterpret_cast<const float *>(smem + wb * SIMT_IMG_MAX);
+            const float *Wi = Wr + f * N_ANT;
+            for (int b = 0; b < tl.nblk; ++b) {
+                const int st = nS % SIMT_NS;
+                if (!bfd::mbar_wait(s_full(st), (nS / SIMT_NS) & 1, abort_flag, p.status)) {
+                    ok = false;
+                    break;
+                }
+                const float *Sb = reinterpret_cast<const float *>(smem + SIMT_OFF_S + st * SIMT_S_STAGE);
+                float ar[8][2], ai[8][2];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
+#pragma unroll 2
+                for (int k = 0; k < f; ++k) {
+                    const float4 s = *reinterpret_cast<const float4 *>(Sb + k * (2 * B_RE) + 4 * jl);
+                    const float4 w0 = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0);
+                    const float4 w1 = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0 + 4);
+                    const float4 v0 = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0);
+                    const float4 v1 = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0 + 4);
+                    const float wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    const float wi[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        ar[r][0] = fmaf(wr[r], s.x, ar[r][0]);
+                        ar[r][0] = fmaf(-wi[r], s.y, ar[r][0]);
+                        ai[r][0] = fmaf(wr[r], s.y, ai[r][0]);
+                        ai[r][0] = fmaf(wi[r], s.x, ai[r][0]);
+                        ar[r][1] = fmaf(wr[r], s.z, ar[r][1]);
+                        ar[r][1] = fmaf(-wi[r], s.w, ar[r][1]);
+                        ai[r][1] = fmaf(wr[r], s.w, ai[r][1]);
+                        ai[r][1] = fmaf(wi[r], s.z, ai[r][1]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) bfd::mbar_arrive(s_empty(st));
+                ++nS;
+                if (lane < 30) {
+                    uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+                        *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
+                            make_float4(ar[r][0], ai[r][0], ar[r][1], ai[r][1]);
+                }
+            }
+            if (ok && (tl.flags & TF_LAST_OF_W)) {
+                __syncwarp();
+                if (lane == 0) bfd::mbar_arrive(w_empty(wb));
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Raise the kernel's dynamic shared-memory limit (once per process, before
+// any launch or graph capture).
+cudaError_t configure_simt() {
+    return cudaFuncSetAttribute(bf_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SIMT_SMEM);
+}
+
+cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream) {
+    bf_simt_kernel<<<n_cta, SIMT_THREADS, SIMT_SMEM, stream>>>(p);
+    return cudaGetLastError();
+}
+
+int simt_smem_bytes() { return SIMT_SMEM; }
+
+}  // namespace bfi

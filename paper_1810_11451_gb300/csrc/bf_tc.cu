@@ -1,0 +1,362 @@
+// bf_tc.cu -- tensor-core forms of R = W x S (Sec. III, beamforming equation)
+// on sm_103a: tcgen05.mma with shared-memory operands, FP32 accumulators in
+// tensor memory, bulk (TMA) copies, mbarrier pipelines.
+//
+// The complex product as one real GEMM, resource elements on M:
+//   D[j][2i+c] = sum_kk A[j][kk] * B[kk][2i+c],  kk = 2k + c'
+//   A[j][2k] = Re S[k][j],  A[j][2k+1] = Im S[k][j]                (M x K)
+//   B[2k][2i] = Re W[i][k], B[2k+1][2i] = -Im W[i][k],
+//   B[2k][2i+1] = Im W[i][k], B[2k+1][2i+1] = Re W[i][k]            (K x N)
+// so D[j][2i] = Re R[i][j] and D[j][2i+1] = Im R[i][j]: tensor-memory lane j
+// holds row j of R^T with real and imaginary parts already interleaved, and a
+// warp's 32 lanes write 32 consecutive resource elements (256 contiguous
+// bytes) of one antenna row of R per store. One MMA tile is M = 128 (two
+// blocks of 60 resource elements, each padded to 64), N = 128 (64 antennas x
+// re/im), K = 2f padded to a multiple of 16.
+//
+// Forms: TERMS = 1 is single pass (bf16 or fp16 operands); TERMS = 3 is the
+// split form Wh*Sh + Wh*Sl + Wl*Sh with x = hi + lo, hi = bf16(x), lo =
+// bf16(x - hi). HELD = false converts complex64 S on chip (raw ring ->
+// converter warps -> operand ring); HELD = true bulk-loads operand images
+// that bf_quantize_symbols encoded beforehand.
+//
+// Warp roles (384 threads, one CTA per SM):
+//   warp 0        bulk-loads S (raw complex64 or held images) into a ring
+//   warp 1        TMEM allocation; one lane issues the MMAs and commits
+//   warp 2        bulk-loads each precoder image once per run of tiles
+//   warps 4..7    (complex64 input) convert raw S into the operand ring
+//   warps 8..11   epilogue: tensor memory -> registers -> global R
+// Tensor memory holds four 128-column accumulators so the MMAs of later
+// tiles overlap the epilogue of earlier ones.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "bf_device.cuh"
+#include "bf_internal.h"
+
+namespace bfi {
+
+constexpr int TC_THREADS = 384;
+constexpr int TC_NACC = 4;       // accumulators in tensor memory
+constexpr int TC_ACC_COLS = 128; // N
+constexpr int TC_RAW_STAGE = 2 * F_LIMIT * S_BYTES_PER_F;  // two complex64 blocks, 34,560 B
+
+template <int TERMS, bool HELD>
+struct TcCfg {
+    static constexpr int A_TERMS = TERMS == 3 ? 2 : 1;  // hi (and lo) operand images
+    static constexpr int W_TERMS = TERMS == 3 ? 2 : 1;
+    static constexpr int NW = (TERMS == 3 && !HELD) ? 1 : 2;
+    static constexpr int NA = HELD ? (TERMS == 3 ? 3 : 4) : (TERMS == 3 ? 2 : 3);
+    static constexpr int NR = HELD ? 0 : (TERMS == 3 ? 2 : 3);
+    static constexpr int W_BUF = W_TERMS * TC_IMG_MAX;
+    static constexpr int A_STAGE = A_TERMS * TC_IMG_MAX;
+    static constexpr int OFF_W = 0;
+    static constexpr int OFF_A = OFF_W + NW * W_BUF;
+    static constexpr int OFF_RAW = OFF_A + NA * A_STAGE;
+    static constexpr int OFF_BAR = OFF_RAW + NR * TC_RAW_STAGE;
+    // raw full/empty, a full/empty, w full/empty, acc full/empty, drain
+    static constexpr int NBARS = 2 * NR + 2 * NA + 2 * NW + 2 * TC_NACC + 1;
+    static constexpr int SMEM = OFF_BAR + NBARS * 8 + 16;
+};
+
+__device__ __forceinline__ uint32_t pack2_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack2_fp16(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float2 unpack2_bf16(uint32_t u) {
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+
+template <int TERMS, bool HELD, bool BF16>
+__global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
+    using C = TcCfg<TERMS, HELD>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + C::NBARS);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + C::NBARS) + 1;
+    const uint32_t bar0 = bfd::smem_u32(bars);
+    auto raw_full = [&](int s) { return bar0 + 8u * s; };
+    auto raw_empty = [&](int s) { return bar0 + 8u * (C::NR + s); };
+    auto a_full = [&](int s) { return bar0 + 8u * (2 * C::NR + s); };
+    auto a_empty = [&](int s) { return bar0 + 8u * (2 * C::NR + C::NA + s); };
+    auto w_full = [&](int s) { return bar0 + 8u * (2 * C::NR + 2 * C::NA + s); };
+    auto w_empty = [&](int s) { return bar0 + 8u * (2 * C::NR + 2 * C::NA + C::NW + s); };
+    auto acc_full = [&](int s) { return bar0 + 8u * (2 * C::NR + 2 * C::NA + 2 * C::NW + s); };
+    auto acc_empty = [&](int s) {
+        return bar0 + 8u * (2 * C::NR + 2 * C::NA + 2 * C::NW + TC_NACC + s);
+    };
+    const uint32_t drain_bar = bar0 + 8u * (C::NBARS - 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
+    constexpr uint32_t IDESC = bfd::idesc_f16(BF16, 128, TC_ACC_COLS);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::NR; ++s) {
+            bfd::mbar_init(raw_full(s), 1);
+            bfd::mbar_init(raw_empty(s), 4);
+        }
+        for (int s = 0; s < C::NA; ++s) {
+            bfd::mbar_init(a_full(s), HELD ? 1 : 4);
+            bfd::mbar_init(a_empty(s), 1);
+        }
+        for (int s = 0; s < C::NW; ++s) {
+            bfd::mbar_init(w_full(s), 1);
+            bfd::mbar_init(w_empty(s), 1);
+        }
+        for (int s = 0; s < TC_NACC; ++s) {
+            bfd::mbar_init(acc_full(s), 1);
+            bfd::mbar_init(acc_empty(s), 4);
+        }
+        bfd::mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        bfd::mbar_init_fence();
+    }
+    if (warp == 1) {
+        bfd::tmem_alloc(bfd::smem_u32(tmem_slot), TC_NACC * TC_ACC_COLS);
+        bfd::tmem_relinquish();
+    }
+    bfd::tc_fence_before();
+    __syncthreads();
+    bfd::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- S producer ----------------
+        if (lane == 0) {
+            int n = 0;
+            for (int t = t0; t < t1; ++t) {
+                const Tile tl = p.tiles[t];
+                if (tl.f == 0) continue;
+                if constexpr (!HELD) {
+                    const int st = n % C::NR;
+                    if (!bfd::mbar_wait(raw_empty(st), ((n / C::NR) + 1) & 1, abort_flag, p.status)) break;
+                    const uint32_t bytes = (uint32_t)(tl.nblk * tl.f * S_BYTES_PER_F);
+                    bfd::mbar_arrive_expect_tx(raw_full(st), bytes);
+                    bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_RAW + st * TC_RAW_STAGE), p.S + tl.s_off,
+                                  bytes, raw_full(st));
+                } else {
+                    const int st = n % C::NA;
+                    if (!bfd::mbar_wait(a_empty(st), ((n / C::NA) + 1) & 1, abort_flag, p.status)) break;
+                    const uint32_t term = 64u * kpad_of(tl.f) * 2u;  // one term of one block
+                    bfd::mbar_arrive_expect_tx(a_full(st), term * C::A_TERMS * tl.nblk);
+                    for (int b = 0; b < tl.nblk; ++b)
+                        for (int q = 0; q < C::A_TERMS; ++q)
+                            bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_A + st * C::A_STAGE + q * TC_IMG_MAX +
+                                                        b * term),
+                                          p.S + tl.s_off + (int64_t)b * term * C::A_TERMS + q * term, term,
+                                          a_full(st));
+                }
+                ++n;
+            }
+            constexpr int NS = HELD ? C::NA : C::NR;
+            for (int m = n > NS ? n - NS : 0; m < n; ++m)
+                bfd::mbar_wait_drain(bar0 + 8u * ((HELD ? 2 * C::NR : 0) + m % NS), (m / NS) & 1,
+                                     1000000000ull);
+        }
+    } else if (warp == 2) {
+        // ---------------- W producer ----------------
+        if (lane == 0) {
+            int n = 0;
+            for (int t = t0; t < t1; ++t) {
+                const Tile tl = p.tiles[t];
+                if (tl.f == 0 || !(tl.flags & TF_FIRST_OF_W)) continue;
+                const int wb = n % C::NW;
+                if (!bfd::mbar_wait(w_empty(wb), ((n / C::NW) + 1) & 1, abort_flag, p.status)) break;
+                const uint32_t bytes = (uint32_t)(C::W_TERMS * tc_img_bytes(kpad_of(tl.f)));
+                bfd::mbar_arrive_expect_tx(w_full(wb), bytes);
+                bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_W + wb * C::W_BUF),
+                              p.w_tc + (int64_t)tl.prec * p.w_tc_stride, bytes, w_full(wb));
+                ++n;
+            }
+            for (int m = n > C::NW ? n - C::NW : 0; m < n; ++m)
+                bfd::mbar_wait_drain(w_full(m % C::NW), (m / C::NW) & 1, 1000000000ull);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int n = 0, nw = 0, wb = 0;
+            for (int t = t0; t < t1; ++t) {
+                const Tile tl = p.tiles[t];
+                if (tl.f == 0) continue;
+                if (tl.flags & TF_FIRST_OF_W) {
+                    wb = nw % C::NW;
+                    if (!bfd::mbar_wait(w_full(wb), (nw / C::NW) & 1, abort_flag, p.status)) break;
+                    ++nw;
+                }
+                const int a = n % C::NA, d = n % TC_NACC;
+                if (!bfd::mbar_wait(a_full(a), (n / C::NA) & 1, abort_flag, p.status)) break;
+                if (!bfd::mbar_wait(acc_empty(d), ((n / TC_NACC) + 1) & 1, abort_flag, p.status)) break;
+                bfd::tc_fence_after();
+                const int kp = kpad_of(tl.f);
+                const uint32_t sbo = 16u * kp;
+                const uint32_t a_hi = bfd::smem_u32(smem + C::OFF_A + a * C::A_STAGE);
+                const uint32_t a_lo = a_hi + TC_IMG_MAX;
+                const uint32_t b_hi = bfd::smem_u32(smem + C::OFF_W + wb * C::W_BUF);
+                const uint32_t b_lo = b_hi + (uint32_t)tc_img_bytes(kp);
+                const uint32_t dt = tmem_base + d * TC_ACC_COLS;
+                for (int s = 0; s < kp / 16; ++s) {
+                    const uint32_t o = 256u * s;  // two 128-byte core matrices along K
+                    bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo), bfd::smem_desc(b_hi + o, 128, sbo),
+                                  IDESC, s > 0 ? 1u : 0u);
+                    if (TERMS == 3) {
+                        bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo),
+                                      bfd::smem_desc(b_lo + o, 128, sbo), IDESC, 1u);
+                        bfd::umma_f16(dt, bfd::smem_desc(a_lo + o, 128, sbo),
+                                      bfd::smem_desc(b_hi + o, 128, sbo), IDESC, 1u);
+                    }
+                }
+                bfd::umma_commit(a_empty(a));
+                bfd::umma_commit(acc_full(d));
+                if (tl.flags & TF_LAST_OF_W) bfd::umma_commit(w_empty(wb));
+                ++n;
+            }
+            // Wait for every MMA issued by this thread before tensor memory is freed.
+            bfd::umma_commit(drain_bar);
+            bfd::mbar_wait_drain(drain_bar, 0, 1000000000ull);
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- converters (complex64 S -> operand images) ----------------
+        if constexpr (!HELD) {
+            const int tid = threadIdx.x - 128;
+            const int blk = tid >> 6, j = tid & 63;
+            int n = 0;
+            for (int t = t0; t < t1; ++t) {
+                const Tile tl = p.tiles[t];
+                const int f = tl.f;
+                if (f == 0) continue;
+                const int r = n % C::NR, a = n % C::NA;
+                if (!bfd::mbar_wait(raw_full(r), (n / C::NR) & 1, abort_flag, p.status)) break;
+                if (!bfd::mbar_wait(a_empty(a), ((n / C::NA) + 1) & 1, abort_flag, p.status)) break;
+                if (blk < tl.nblk && j < B_RE) {
+                    const uint8_t *raw = smem + C::OFF_RAW + r * TC_RAW_STAGE + blk * f * S_BYTES_PER_F;
+                    const int kp = kpad_of(f);
+                    const int row = 64 * blk + j;
+                    uint8_t *dst = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
+                    for (int q = 0; q < kp / 8; ++q) {
+                        float v[8];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = 4 * q + u;
+                            float2 x = make_float2(0.f, 0.f);
+                            if (k < f) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F + j * 8);
+                            v[2 * u] = x.x;
+                            v[2 * u + 1] = x.y;
+                        }
+                        uint4 hi, lo;
+                        uint32_t *h = &hi.x, *l = &lo.x;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (BF16) {
+                                h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
+                                if (TERMS == 3) {
+                                    const float2 back = unpack2_bf16(h[u]);
+                                    l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
+                                }
+                            } else {
+                                h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
+                            }
+                        }
+                        *reinterpret_cast<uint4 *>(dst + q * 128) = hi;
+                        if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + TC_IMG_MAX + q * 128) = lo;
+                    }
+                }
+                bfd::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bfd::mbar_arrive(raw_empty(r));
+                    bfd::mbar_arrive(a_full(a));
+                }
+                ++n;
+            }
+        }
+    } else if (warp >= 8) {
+        // ---------------- epilogue ----------------
+        const int q = warp - 8;               // tensor-memory lane quadrant
+        const int blk = q >> 1;               // block of the tile
+        const int j = (q & 1) * 32 + lane;    // resource element
+        int n = 0;
+        for (int t = t0; t < t1; ++t) {
+            const Tile tl = p.tiles[t];
+            const bool live = blk < tl.nblk && j < B_RE;
+            float2 *rrow = reinterpret_cast<float2 *>(p.R + tl.r_off + (int64_t)blk * R_BLOCK_BYTES) + j;
+            if (tl.f == 0) {
+                if (live)
+                    for (int i = 0; i < N_ANT; ++i) rrow[i * B_RE] = make_float2(0.f, 0.f);
+                continue;
+            }
+            const int d = n % TC_NACC;
+            if (!bfd::mbar_wait(acc_full(d), (n / TC_NACC) & 1, abort_flag, p.status)) break;
+            bfd::tc_fence_after();
+            float scale = p.w_scale[tl.prec];
+            if (HELD) scale *= p.s_scale[tl.sblk + (blk < tl.nblk ? blk : 0)];
+            const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + d * TC_ACC_COLS;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                uint32_t v[32];
+                bfd::tmem_ld32(ta + 32 * c, v);
+                bfd::tmem_ld_wait();
+                if (live) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        rrow[(16 * c + u) * B_RE] =
+                            make_float2(__uint_as_float(v[2 * u]) * scale, __uint_as_float(v[2 * u + 1]) * scale);
+                }
+            }
+            bfd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bfd::mbar_arrive(acc_empty(d));
+            ++n;
+        }
+    }
+
+    __syncthreads();
+    if (warp == 1) {
+        bfd::tc_fence_after();
+        bfd::tmem_dealloc(tmem_base, TC_NACC * TC_ACC_COLS);
+    }
+}
+
+template <int TERMS, bool HELD, bool BF16>
+static cudaError_t configure_tc_t() {
+    return cudaFuncSetAttribute(bf_tc_kernel<TERMS, HELD, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<TERMS, HELD>::SMEM);
+}
+
+template <int TERMS, bool HELD, bool BF16>
+static cudaError_t launch_tc_t(const KParams &p, int n_cta, cudaStream_t stream) {
+    bf_tc_kernel<TERMS, HELD, BF16><<<n_cta, TC_THREADS, TcCfg<TERMS, HELD>::SMEM, stream>>>(p);
+    return cudaGetLastError();
+}
+
+// Raise every instance's dynamic shared-memory limit (once, before launches).
+cudaError_t configure_tc() {
+    cudaError_t e;
+    if ((e = configure_tc_t<3, true, true>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<3, false, true>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, true, true>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, false, true>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, true, false>()) != cudaSuccess) return e;
+    return configure_tc_t<1, false, false>();
+}
+
+// prec: BF_BF16, BF_FP16 or BF_BF16X3.
+cudaError_t launch_tc(int prec, bool held, const KParams &p, int n_cta, cudaStream_t stream) {
+    if (prec == BF_BF16X3) return held ? launch_tc_t<3, true, true>(p, n_cta, stream)
+                                       : launch_tc_t<3, false, true>(p, n_cta, stream);
+    if (prec == BF_BF16) return held ? launch_tc_t<1, true, true>(p, n_cta, stream)
+                                     : launch_tc_t<1, false, true>(p, n_cta, stream);
+    return held ? launch_tc_t<1, true, false>(p, n_cta, stream) : launch_tc_t<1, false, false>(p, n_cta, stream);
+}
+
+int tc_smem_bytes(int prec, bool held) {
+    if (prec == BF_BF16X3) return held ? TcCfg<3, true>::SMEM : TcCfg<3, false>::SMEM;
+    return held ? TcCfg<1, true>::SMEM : TcCfg<1, false>::SMEM;
+}
+
+}  // namespace bfi

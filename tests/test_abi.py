@@ -1,0 +1,154 @@
+"""CPU checks of the C ABI: the library loads and exports every declared symbol,
+argument checks that precede any CUDA call, and the host-side scheduler."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bf():
+    from paper_1810_11451_gb300 import build
+    build.build()
+    import paper_1810_11451_gb300 as m
+    m.lib()
+    return m
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?[\s\*]+(bf_[a-z0-9_]+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(bf):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(bf.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(bf):
+    for n in declared_functions():
+        assert hasattr(bf, n), f"binding lacks {n}"
+
+
+def test_plan_create_rejects_shapes_before_cuda(bf):
+    for args in [(32, 36, 60), (64, 37, 60), (64, -1, 60), (64, 36, 64)]:
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_plan_create(*args)
+        assert ei.value.status == bf.BF_EINVAL
+    assert "n_ant" in bf.bf_last_error(None) or "b must" in bf.bf_last_error(None)
+
+
+def test_status_strings(bf):
+    assert bf.bf_status_string(bf.BF_OK) == "BF_OK"
+    assert bf.bf_status_string(bf.BF_ETIMEOUT) == "BF_ETIMEOUT"
+    assert bf.bf_status_string(99) == "BF_UNKNOWN"
+
+
+def test_held_block_bytes(bf):
+    for f in range(0, 37):
+        k = ((2 * f + 15) // 16) * 16
+        assert bf.bf_held_block_bytes(f, bf.BF_BF16) == 128 * k
+        assert bf.bf_held_block_bytes(f, bf.BF_FP16) == 128 * k
+        assert bf.bf_held_block_bytes(f, bf.BF_BF16X3) == 256 * k
+        assert bf.bf_held_block_bytes(f, bf.BF_FP32) == 0
+    assert bf.bf_held_block_bytes(37, bf.BF_BF16) == 0
+
+
+def test_missing_library_fails_loudly(bf, monkeypatch):
+    monkeypatch.setattr(bf, "LIB_PATH", "/nonexistent/libbf.so")
+    monkeypatch.setattr(bf, "_lib", None)
+    with pytest.raises(ImportError):
+        bf.lib()
+
+
+class BfTile(ctypes.Structure):
+    _fields_ = [("s_off", ctypes.c_int64), ("r_off", ctypes.c_int64), ("prec_id", ctypes.c_int32),
+                ("first_block", ctypes.c_int32), ("f", ctypes.c_int16), ("n_blocks", ctypes.c_int16),
+                ("flags", ctypes.c_int32)]
+
+
+def schedule(bf, f_of_slot, groups, prec, held, max_cta):
+    L = bf.lib()
+    L.bf_schedule.restype = ctypes.c_int32
+    fa = (ctypes.c_int32 * len(f_of_slot))(*f_of_slot)
+    ga, n = bf.make_groups(groups)
+    ncta = ctypes.c_int32()
+    nt = L.bf_schedule(fa, len(f_of_slot), ga, n, prec, held, max_cta, None, 0, None, ctypes.byref(ncta))
+    assert nt >= 0
+    tiles = (BfTile * max(1, nt))()
+    begin = (ctypes.c_int32 * (max_cta + 1))()
+    nt2 = L.bf_schedule(fa, len(f_of_slot), ga, n, prec, held, max_cta, tiles, nt, begin, ctypes.byref(ncta))
+    assert nt2 == nt
+    return list(tiles)[:nt], list(begin)[:ncta.value + 1]
+
+
+@pytest.mark.parametrize("max_cta", [1, 7, 152, 10000])
+def test_scheduler_covers_every_block_once(bf, max_cta):
+    batch = wl.config_uneven(seed=3, n_blocks=1500)
+    from bfrun import layout
+    groups = layout(batch).groups
+    f_of_slot = batch.f_of_group
+    tiles, begin = schedule(bf, f_of_slot, groups, bf.BF_BF16X3, 0, max_cta)
+    # every block exactly once, in group order, tiles of <= 2 blocks of one group
+    seen = []
+    for t in tiles:
+        assert 1 <= t.n_blocks <= 2 and t.f == f_of_slot[t.prec_id]
+        seen += list(range(t.first_block, t.first_block + t.n_blocks))
+    assert seen == list(range(batch.total_blocks))
+    # offsets follow the group layout
+    blk_group = np.repeat(np.arange(len(groups)), batch.n_blocks)
+    first_in_group = np.cumsum([0] + batch.n_blocks[:-1])
+    for t in tiles:
+        g = blk_group[t.first_block]
+        n = t.first_block - first_in_group[g]
+        assert t.s_off == groups[g][2] + n * 480 * batch.f_of_group[g]
+        assert t.r_off == groups[g][3] + n * 30720
+    # contiguous CTA ranges covering all tiles, none empty
+    assert begin[0] == 0 and begin[-1] == len(tiles)
+    assert all(begin[c] < begin[c + 1] for c in range(len(begin) - 1))
+    assert len(begin) - 1 == min(max_cta, len(tiles))
+    # cost balance: no CTA above the mean by more than one tile's cost
+    cost = np.array([t.n_blocks * (480 * t.f + 30720) for t in tiles], float)
+    per = [cost[begin[c]:begin[c + 1]].sum() for c in range(len(begin) - 1)]
+    assert max(per) <= cost.sum() / len(per) + 2 * cost.max()
+    # precoder-run flags
+    for c in range(len(begin) - 1):
+        run = [t for t in tiles[begin[c]:begin[c + 1]] if t.f > 0]
+        for i, t in enumerate(run):
+            first = i == 0 or run[i - 1].prec_id != t.prec_id
+            last = i == len(run) - 1 or run[i + 1].prec_id != t.prec_id
+            assert bool(t.flags & 1) == first and bool(t.flags & 2) == last
+
+
+def test_scheduler_rejects_bad_input(bf):
+    L = bf.lib()
+    fa = (ctypes.c_int32 * 2)(8, 40)
+    ga, n = bf.make_groups([(1, 2, 0, 0)])
+    ncta = ctypes.c_int32()
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    ga, n = bf.make_groups([(5, 2, 0, 0)])
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    ga, n = bf.make_groups([(0, 2, 0, 0)])
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 1, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == 1
+
+
+def test_scheduler_empty_and_zero_f(bf):
+    tiles, begin = schedule(bf, [0, 3], [(0, 3, 0, 0), (1, 0, 0, 0)], bf.BF_FP32, 0, 4)
+    assert [t.n_blocks for t in tiles] == [2, 1] and all(t.flags == 0 for t in tiles)
+    tiles, begin = schedule(bf, [3], [], bf.BF_FP32, 0, 4)
+    assert tiles == [] and begin == [0, 0]

@@ -1,0 +1,238 @@
+"""GPU parity of every product form against the FP64 oracle, through the C ABI.
+
+Tolerances (relative Frobenius error over the batch, from the accuracy target
+of the method's reduced-precision study): <= 1e-5 for the FP32 plain form and
+the split-bf16 form, <= 2e-2 for single-pass bf16/fp16 (measured against the
+unrounded FP64 inputs, so the bound covers the operand rounding). Exact-integer
+inputs (odd-integer QAM, Gaussian-integer W in {-2..2}) make every product and
+partial sum exact in bf16, fp16 and fp32, so there every form must match the
+oracle bit for bit. R is NaN-poisoned before each run, so unwritten elements
+(including f = 0 blocks and ragged tiles) fail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1810_11451_gb300 as bf  # noqa: E402
+from bfrun import layout, run, set_precoders  # noqa: E402
+
+TOL_FP32 = 1e-5
+TOL_SPLIT = 1e-5
+TOL_SINGLE = 2e-2
+FORMS = [("fp32", bf.BF_FP32, False), ("bf16x3", bf.BF_BF16X3, False), ("bf16x3_held", bf.BF_BF16X3, True),
+         ("bf16", bf.BF_BF16, False), ("bf16_held", bf.BF_BF16, True), ("fp16", bf.BF_FP16, False),
+         ("fp16_held", bf.BF_FP16, True)]
+
+
+@pytest.fixture(scope="module")
+def plan():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    p = bf.bf_plan_create(64, 36, 60)
+    yield p
+    assert bf.bf_device_status(p) == bf.BF_OK
+    bf.bf_plan_destroy(p)
+
+
+def _ref(batch):
+    return oracle.apply_batch(batch.rounded(np.complex64))
+
+
+def _tol(prec):
+    return {bf.BF_FP32: TOL_FP32, bf.BF_BF16X3: TOL_SPLIT}.get(prec, TOL_SINGLE)
+
+
+def _assert_close(R, ref, tol, what):
+    assert all(np.all(np.isfinite(r)) for r in R), f"{what}: unwritten (NaN) outputs"
+    e = oracle.rel_frobenius(R, ref)
+    assert e <= tol, f"{what}: relative Frobenius error {e:.3e} > {tol:.1e}"
+    return e
+
+
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
+def test_exact_integers_bitwise(plan, name, prec, held):
+    batch = wl.config_exact_integer()
+    R = run(plan, batch, prec, torch, held=held)
+    ref = oracle.apply_batch(batch)
+    for g, (a, r) in enumerate(zip(R, ref)):
+        assert np.array_equal(a.astype(np.complex128), r), \
+            f"{name}: group {g} (f={batch.f_of_group[g]}, nb={batch.n_blocks[g]}) differs"
+
+
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
+def test_small_config(plan, name, prec, held):
+    """One 64x8 precoder, 16-QAM blocks (the small FP32 workload, 300 blocks)."""
+    batch = wl.config_small(seed=0, n_blocks=300)
+    R = run(plan, batch, prec, torch, held=held)
+    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    _assert_close(R, ref, _tol(prec), name)
+
+
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
+def test_fullband_scaled(plan, name, prec, held):
+    """f = 36, 13 resource blocks x 14 symbols (odd tile counts per CTA run)."""
+    batch = wl.config_fullband(seed=2, n_rb=13, n_sym=14)
+    R = run(plan, batch, prec, torch, held=held)
+    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    e = _assert_close(R, ref, _tol(prec), name)
+    if prec in (bf.BF_FP32, bf.BF_BF16X3):
+        for g, (a, r) in enumerate(zip(R, ref)):
+            num, den = oracle.errnorm_blocks(a, r)
+            assert np.all(np.sqrt(num / den) <= _tol(prec)), f"{name}: group {g} per-block error"
+    print(f"{name}: rel err {e:.3e}")
+
+
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[2], FORMS[4]],
+                         ids=["fp32", "bf16x3", "bf16x3_held", "bf16_held"])
+def test_uneven_scaled(plan, name, prec, held):
+    """Uneven f (0..36) per group, geometric group sizes, mixed QAM orders."""
+    batch = wl.config_uneven(seed=3, n_blocks=700)
+    R = run(plan, batch, prec, torch, held=held)
+    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    for a, f in zip(R, batch.f_of_group):
+        if f == 0:
+            assert np.all(a == 0)
+    _assert_close(R, ref, _tol(prec), name)
+
+
+@pytest.mark.parametrize("prec,name", [(bf.BF_BF16, "bf16"), (bf.BF_FP16, "fp16"), (bf.BF_BF16X3, "bf16x3")])
+def test_quantize_bit_exact(plan, prec, name):
+    """Held S is the oracle's encoding, bit for bit (scale, rounding, layout, zero padding)."""
+    batch = wl.config_reduced(seed=4, copies=1, n_rb=3, n_sym=3, f=17)
+    _, bufs = run(plan, batch, prec, torch, held=True, return_buffers=True)
+    lay = layout(batch, 0, prec)
+    raw = bufs["S"].cpu().numpy().view(np.uint16)
+    scales = bufs["scale"].cpu().numpy()
+    f = 17
+    kp = ((2 * f + 15) // 16) * 16
+    term = 64 * kp
+    blk = 0
+    for g, S in enumerate(batch.S):
+        for n in range(S.shape[0]):
+            s, planes = oracle.quantize_planes(S[n].astype(np.complex64), name)
+            assert scales[blk] == np.float32(s)
+            base = (lay.held_off[g] + n * bf.bf_held_block_bytes(f, prec)) // 2
+            for t, (re, im) in enumerate(planes):
+                img = np.zeros((64, kp), np.float32)
+                img[:60, 0:2 * f:2] = re.T
+                img[:60, 1:2 * f:2] = im.T
+                bits = (oracle.bf16_bits(img) if name != "fp16"
+                        else img.astype(np.float16).view(np.uint16))
+                rows, cols = np.meshgrid(np.arange(64), np.arange(kp), indexing="ij")
+                off = (rows // 8) * (8 * kp) + (cols // 8) * 64 + (rows % 8) * 8 + (cols % 8)
+                got = raw[base + t * term + off]
+                assert np.array_equal(got, bits), f"block {blk} term {t} differs"
+            blk += 1
+
+
+@pytest.mark.parametrize("prec,name", [(bf.BF_BF16, "bf16"), (bf.BF_FP16, "fp16"), (bf.BF_BF16X3, "bf16x3")])
+def test_reduced_mechanics(plan, prec, name):
+    """Held forms against the FP64 product of the encoded operands: only FP32
+    accumulation rounding separates them."""
+    batch = wl.config_reduced(seed=4, copies=1, n_rb=9, n_sym=5)
+    R = run(plan, batch, prec, torch, held=True)
+    for g, (p, S) in enumerate(zip(batch.prec, batch.S)):
+        W = batch.W[p].astype(np.complex64)
+        sw, wpl = oracle.quantize_planes(W, name)
+        Wt = [a + 1j * b for a, b in wpl]
+        pairs = [(0, 0)] if name != "bf16x3" else [(0, 0), (0, 1), (1, 0)]
+        exp = np.empty((S.shape[0], 64, 60), np.complex128)
+        for n in range(S.shape[0]):
+            ss, spl = oracle.quantize_planes(S[n].astype(np.complex64), name)
+            St = [(a + 1j * b)[None] for a, b in spl]
+            exp[n] = oracle.apply_terms(Wt, St, pairs, sw * ss)[0]
+        e = oracle.rel_frobenius([R[g]], [exp])
+        assert e < 2e-6, f"{name}: group {g} mechanics error {e:.2e}"
+
+
+def test_reduced_accuracy(plan):
+    """The reduced-precision workload (256-QAM + noise, f = 36), scaled down."""
+    batch = wl.config_reduced(seed=4, copies=1, n_rb=20, n_sym=14)
+    ref64 = oracle.apply_batch(batch)
+    ref32 = _ref(batch)
+    errs = {}
+    for name, prec, held in FORMS[1:]:
+        R = run(plan, batch, prec, torch, held=held)
+        errs[name] = _assert_close(R, ref32 if prec == bf.BF_BF16X3 else ref64, _tol(prec), name)
+    print("reduced-precision errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+
+
+def test_graph_and_host_paths_bitwise(plan):
+    """The graph-captured batch and the host-buffer pipeline give the same bits."""
+    batch = wl.config_uneven(seed=9, n_blocks=400)
+    for prec in (bf.BF_FP32, bf.BF_BF16X3):
+        a = run(plan, batch, prec, torch, mode="apply")
+        b = run(plan, batch, prec, torch, mode="batch", set_w=False)
+        c = run(plan, batch, prec, torch, mode="host", set_w=False)
+        d = run(plan, batch, prec, torch, mode="apply", set_w=False)
+        for x, y, z, w in zip(a, b, c, d):
+            assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+            assert np.array_equal(x.view(np.uint64), z.view(np.uint64))
+            assert np.array_equal(x.view(np.uint64), w.view(np.uint64))
+
+
+def test_fullband_full_size(plan):
+    """The full-band f = 36 workload at full size (273 x 14 = 3,822 blocks) in
+    the launch configuration the bench times, checked in full against the oracle."""
+    batch = wl.config_fullband()
+    ref = _ref(batch)
+    for prec in (bf.BF_FP32, bf.BF_BF16X3):
+        R = run(plan, batch, prec, torch, mode="batch")
+        e = _assert_close(R, ref, _tol(prec), f"fullband prec {prec}")
+        print(f"full band prec {prec}: rel err {e:.3e}")
+
+
+def test_errnorm_matches_numpy(plan):
+    rng = np.random.default_rng(5)
+    n = 37
+    Rref = rng.normal(size=(n, 64, 60)) + 1j * rng.normal(size=(n, 64, 60))
+    R = (Rref + 1e-3 * (rng.normal(size=Rref.shape) + 1j * rng.normal(size=Rref.shape))).astype(np.complex64)
+    Rd = torch.from_numpy(np.ascontiguousarray(R).view(np.float32)).cuda()
+    Rrefd = torch.from_numpy(np.ascontiguousarray(Rref).view(np.float64)).cuda()
+    per = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    num, den = bf.bf_errnorm(plan, Rd, Rrefd, n, per)
+    enum, eden = oracle.errnorm_blocks(R, Rref)
+    assert np.isclose(num, enum.sum(), rtol=1e-12) and np.isclose(den, eden.sum(), rtol=1e-12)
+    p = per.cpu().numpy().reshape(n, 2)
+    assert np.allclose(p[:, 0], enum, rtol=1e-12) and np.allclose(p[:, 1], eden, rtol=1e-12)
+    assert bf.bf_errnorm(plan, Rd, Rrefd, 0) == (0.0, 0.0)
+
+
+def test_edge_cases_and_errors(plan):
+    batch = wl.config_small(seed=1, n_blocks=3, f=5)
+    set_precoders(plan, batch, torch, slot_base=100)
+    R_t = torch.zeros(3 * 64 * 60 * 2, device="cuda")
+    S_t = torch.zeros(3 * 5 * 60 * 2, device="cuda")
+    # empty batch and empty group
+    bf.bf_apply_batch(plan, S_t, None, [], bf.BF_FP32, R_t)
+    bf.bf_apply_batch(plan, S_t, None, [(100, 0, 0, 0)], bf.BF_FP32, R_t)
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_apply_batch(plan, S_t, None, [(4000, 1, 0, 0)], bf.BF_FP32, R_t)  # unset slot
+    assert ei.value.status == bf.BF_ENOTFOUND
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_apply_batch(plan, S_t, None, [(100, 1, 8, 0)], bf.BF_FP32, R_t)  # misaligned offset
+    assert ei.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_apply_batch(plan, S_t.data_ptr() + 4, None, [(100, 1, 0, 0)], bf.BF_FP32, R_t)
+    assert ei.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_apply_batch(plan, S_t, R_t, [(100, 1, 0, 0)], bf.BF_FP32, R_t)  # FP32 takes no scale
+    assert ei.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_set_precoders(plan, S_t, [37], 0)  # f > f_max
+    assert ei.value.status == bf.BF_EINVAL
+    assert bf.bf_device_status(plan) == bf.BF_OK
+
+
+def test_deterministic(plan):
+    batch = wl.config_fullband(seed=6, n_rb=7, n_sym=14)
+    for prec in (bf.BF_FP32, bf.BF_BF16X3, bf.BF_BF16):
+        a = run(plan, batch, prec, torch)
+        b = run(plan, batch, prec, torch, set_w=False)
+        assert all(np.array_equal(x.view(np.uint64), y.view(np.uint64)) for x, y in zip(a, b))
