@@ -215,6 +215,112 @@ def bf_plan_launch_count(plan) -> int:
     return int(lib().bf_plan_launch_count(plan))
 
 
+# ---------------------------------------------------------------- serving (bf_serve.h)
+class bf_serve_config(ctypes.Structure):
+    _fields_ = [("n_slots", c_int32), ("max_batch_jobs", c_int32), ("queue_capacity", c_int32),
+                ("fake_device_us", c_int32), ("hbm_budget_bytes", c_int64)]
+
+
+class bf_job(ctypes.Structure):
+    _fields_ = [("cell", c_int32), ("n_groups", c_int32), ("groups", POINTER(bf_group)), ("prec", c_int32),
+                ("pad", c_int32), ("S_dev", c_void_p), ("R_dev", c_void_p), ("arrival_ns", c_int64)]
+
+
+class bf_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("launches", c_int64),
+                ("rejected_budget", c_int64), ("rejected_full", c_int64), ("budget_waits", c_int64),
+                ("max_inflight_bytes", c_int64), ("max_busy_slots", c_int32), ("max_jobs_per_launch", c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _serve_sigs(L):
+    if getattr(L, "_serve_sigs", False):
+        return L
+    for name, res, args in [
+        ("bf_now_ns", c_int64, []),
+        ("bf_serve_create", c_int, [c_void_p, POINTER(bf_serve_config), POINTER(c_void_p)]),
+        ("bf_serve_destroy", c_int, [c_void_p, c_int64]),
+        ("bf_serve_set_precoders", c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32]),
+        ("bf_submit", c_int, [c_void_p, POINTER(bf_job), POINTER(ctypes.c_uint64)]),
+        ("bf_poll", c_int, [c_void_p, ctypes.c_uint64, POINTER(c_int), POINTER(c_double)]),
+        ("bf_wait", c_int, [c_void_p, ctypes.c_uint64, c_int64, POINTER(c_double)]),
+        ("bf_serve_pause", c_int, [c_void_p, c_int32]),
+        ("bf_serve_get_stats", c_int, [c_void_p, POINTER(bf_serve_stats)]),
+    ]:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    L._serve_sigs = True
+    return L
+
+
+def bf_now_ns() -> int:
+    return int(_serve_sigs(lib()).bf_now_ns())
+
+
+def bf_serve_create(plan, n_slots: int = 4, max_batch_jobs: int = 16, queue_capacity: int = 4096,
+                    hbm_budget_bytes: int = 8 << 30, fake_device_us: int = 0) -> int:
+    L = _serve_sigs(lib())
+    cfg = bf_serve_config(n_slots, max_batch_jobs, queue_capacity, fake_device_us, hbm_budget_bytes)
+    h = c_void_p()
+    _check(L.bf_serve_create(plan, ctypes.byref(cfg), ctypes.byref(h)), plan)
+    return h.value
+
+
+def bf_serve_destroy(srv, timeout_us: int = 10_000_000) -> None:
+    st = _serve_sigs(lib()).bf_serve_destroy(srv, int(timeout_us))
+    if st != BF_OK:
+        raise BfError(st, "bf_serve_destroy: jobs still queued or running")
+
+
+def bf_serve_set_precoders(srv, W_dev, f_list: Sequence[int], first_id: int = 0) -> None:
+    fa = (c_int32 * max(1, len(f_list)))(*[int(f) for f in f_list])
+    st = _serve_sigs(lib()).bf_serve_set_precoders(srv, _ptr(W_dev), fa, len(f_list), int(first_id))
+    if st != BF_OK:
+        raise BfError(st, "bf_serve_set_precoders failed")
+
+
+def bf_submit(srv, groups, prec: int, S_dev, R_dev, cell: int = 0, arrival_ns: int = 0) -> int:
+    """Queue a job; returns its ticket. Raises BfError (status BF_EBUDGET,
+    BF_EAGAIN, BF_ENOTFOUND, BF_EINVAL) when it is refused."""
+    ga, n = make_groups(groups)
+    job = bf_job(int(cell), n, ga, int(prec), 0, _ptr(S_dev), _ptr(R_dev), int(arrival_ns))
+    t = ctypes.c_uint64()
+    st = _serve_sigs(lib()).bf_submit(srv, ctypes.byref(job), ctypes.byref(t))
+    if st != BF_OK:
+        raise BfError(st, bf_last_error(None))
+    return int(t.value)
+
+
+def bf_poll(srv, ticket: int) -> Tuple[bool, Optional[float]]:
+    """(done, latency_us); the ticket is retired once done is returned True."""
+    d, lat = c_int(), c_double()
+    st = _serve_sigs(lib()).bf_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(lat))
+    if st != BF_OK:
+        raise BfError(st, "bf_poll")
+    return bool(d.value), (float(lat.value) if d.value else None)
+
+
+def bf_wait(srv, ticket: int, timeout_us: int) -> float:
+    lat = c_double()
+    st = _serve_sigs(lib()).bf_wait(srv, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(lat))
+    if st != BF_OK:
+        raise BfError(st, "bf_wait")
+    return float(lat.value)
+
+
+def bf_serve_pause(srv, paused: bool) -> None:
+    _serve_sigs(lib()).bf_serve_pause(srv, int(bool(paused)))
+
+
+def bf_serve_get_stats(srv) -> dict:
+    s = bf_serve_stats()
+    _check(_serve_sigs(lib()).bf_serve_get_stats(srv, ctypes.byref(s)))
+    return s.as_dict()
+
+
 class bf_tile(ctypes.Structure):
     """One scheduled work item (see bf_schedule in bf.h)."""
     _fields_ = [("s_off", c_int64), ("r_off", c_int64), ("prec_id", c_int32), ("first_block", c_int32),

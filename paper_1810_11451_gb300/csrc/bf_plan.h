@@ -59,7 +59,7 @@ struct bf_plan_s {
     float *w_scale = nullptr;
     int *d_status = nullptr;
     // work-list ring
-    bfi::WorkBuf ring[8];
+    bfi::WorkBuf ring[16];
     int ring_next = 0;
     bfi::WorkList scratch_wl;
     // prep staging

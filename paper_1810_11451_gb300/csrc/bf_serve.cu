@@ -1,0 +1,386 @@
+// bf_serve.cu -- the continuous-batching serving loop of include/bf_serve.h:
+// FIFO queue, HBM-budget admission, launch slots (one stream each), merged
+// launches of the persistent product kernel, completion by event polling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bf_internal.h"
+#include "bf_plan.h"
+#include "bf_serve.h"
+
+using namespace bfi;
+
+namespace {
+
+enum JobState { QUEUED = 0, RUNNING = 1, DONE = 2 };
+
+struct JobRec {
+    int cell = 0;
+    bf_precision prec = BF_FP32;
+    std::vector<bf_group> groups;  // absolute byte addresses in s_off / r_off
+    int64_t bytes = 0;
+    int64_t arrival_ns = 0;
+    int64_t done_ns = 0;
+    int state = QUEUED;
+    bool waited_budget = false;
+    bf_status status = BF_OK;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    int64_t fake_done_ns = 0;
+    std::vector<uint64_t> jobs;
+};
+
+}  // namespace
+
+struct bf_server_s {
+    bf_plan plan = nullptr;
+    bf_serve_config cfg{};
+    bool fake = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, JobRec> jobs;
+    std::vector<Slot> slots;
+    int64_t inflight_bytes = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false, paused = false, exited = false;
+    std::thread th;
+    bf_serve_stats stats{};
+    std::mutex plan_mu;  // the plan is used by the dispatcher and bf_serve_set_precoders
+    cudaStream_t prep_st = nullptr;
+    cudaEvent_t prep_ev = nullptr;
+    bool prep_used = false;
+    std::vector<bf_group> merged;
+};
+
+extern "C" int64_t bf_now_ns(void) {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+static int64_t job_bytes(const int *f_slot, const bf_job *job) {
+    int64_t b = 0;
+    for (int g = 0; g < job->n_groups; ++g) {
+        const int f = f_slot ? f_slot[job->groups[g].prec_id] : 0;
+        b += (int64_t)job->groups[g].n_blocks * ((int64_t)f * S_BYTES_PER_F + R_BLOCK_BYTES);
+    }
+    return b;
+}
+
+// Launch one merged batch on a slot (called without the queue lock).
+static bf_status launch_slot(bf_server srv, Slot &slot, bf_precision prec, const std::vector<bf_group> &groups) {
+    if (srv->fake) {
+        slot.fake_done_ns = bf_now_ns() + (int64_t)srv->cfg.fake_device_us * 1000;
+        return BF_OK;
+    }
+    std::lock_guard<std::mutex> pl(srv->plan_mu);
+    bf_plan plan = srv->plan;
+    if (srv->prep_used && cudaStreamWaitEvent(slot.st, srv->prep_ev, 0) != cudaSuccess)
+        return bf_fail(plan, BF_ECUDA, "cudaStreamWaitEvent failed");
+    // S and R bases are 0: the groups carry absolute device addresses, so jobs
+    // with different buffers share one launch.
+    bf_status s = enqueue_apply(plan, nullptr, nullptr, groups.data(), (int32_t)groups.size(), prec, nullptr,
+                                slot.st, 0);
+    if (s != BF_OK) return s;
+    if (cudaEventRecord(slot.ev, slot.st) != cudaSuccess) return bf_fail(plan, BF_ECUDA, "cudaEventRecord failed");
+    return BF_OK;
+}
+
+static void dispatcher(bf_server srv) {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        bool any_busy = false, progressed = false;
+        // 1. completions
+        const int64_t now = bf_now_ns();
+        for (Slot &sl : srv->slots) {
+            if (!sl.busy) continue;
+            bool done;
+            bf_status st = BF_OK;
+            if (srv->fake) {
+                done = now >= sl.fake_done_ns;
+            } else {
+                const cudaError_t e = cudaEventQuery(sl.ev);
+                done = e != cudaErrorNotReady;
+                if (done && e != cudaSuccess) st = BF_ECUDA;
+            }
+            if (!done) {
+                any_busy = true;
+                continue;
+            }
+            for (uint64_t t : sl.jobs) {
+                JobRec &j = srv->jobs[t];
+                j.state = DONE;
+                j.status = st;
+                j.done_ns = now;
+                srv->inflight_bytes -= j.bytes;
+                srv->stats.completed++;
+            }
+            sl.jobs.clear();
+            sl.busy = false;
+            progressed = true;
+            srv->cv_done.notify_all();
+        }
+        // 2. admission: FIFO, one precision per launch, within the budget
+        while (!srv->paused && !srv->queue.empty()) {
+            Slot *free_slot = nullptr;
+            for (Slot &sl : srv->slots)
+                if (!sl.busy) {
+                    free_slot = &sl;
+                    break;
+                }
+            if (!free_slot) break;
+            JobRec &head = srv->jobs[srv->queue.front()];
+            if (srv->inflight_bytes + head.bytes > srv->cfg.hbm_budget_bytes) {
+                if (!head.waited_budget) {
+                    head.waited_budget = true;
+                    srv->stats.budget_waits++;
+                }
+                break;
+            }
+            const bf_precision prec = head.prec;
+            std::vector<uint64_t> take;
+            int64_t add = 0;
+            while (!srv->queue.empty() && (int)take.size() < srv->cfg.max_batch_jobs) {
+                JobRec &j = srv->jobs[srv->queue.front()];
+                if (j.prec != prec || srv->inflight_bytes + add + j.bytes > srv->cfg.hbm_budget_bytes) break;
+                take.push_back(srv->queue.front());
+                add += j.bytes;
+                srv->queue.pop_front();
+            }
+            srv->merged.clear();
+            for (uint64_t t : take) {
+                JobRec &j = srv->jobs[t];
+                j.state = RUNNING;
+                srv->merged.insert(srv->merged.end(), j.groups.begin(), j.groups.end());
+            }
+            srv->inflight_bytes += add;
+            srv->stats.max_inflight_bytes = std::max(srv->stats.max_inflight_bytes, srv->inflight_bytes);
+            free_slot->busy = true;
+            free_slot->jobs = take;
+            std::vector<bf_group> groups;
+            groups.swap(srv->merged);
+            lk.unlock();
+            const bf_status st = launch_slot(srv, *free_slot, prec, groups);
+            lk.lock();
+            srv->stats.launches++;
+            srv->stats.max_jobs_per_launch = std::max(srv->stats.max_jobs_per_launch, (int32_t)take.size());
+            int busy = 0;
+            for (Slot &sl : srv->slots) busy += sl.busy ? 1 : 0;
+            srv->stats.max_busy_slots = std::max(srv->stats.max_busy_slots, busy);
+            if (st != BF_OK) {  // the launch failed: complete its jobs with the error
+                for (uint64_t t : take) {
+                    JobRec &j = srv->jobs[t];
+                    j.state = DONE;
+                    j.status = st;
+                    j.done_ns = bf_now_ns();
+                    srv->inflight_bytes -= j.bytes;
+                    srv->stats.completed++;
+                }
+                free_slot->jobs.clear();
+                free_slot->busy = false;
+                srv->cv_done.notify_all();
+            }
+            any_busy = true;
+            progressed = true;
+        }
+        if (srv->stop && srv->queue.empty() && !any_busy) break;
+        if (!any_busy && (srv->queue.empty() || srv->paused)) {
+            srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+        } else if (!progressed) {
+            // launches in flight: poll completion with short pauses
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(2));
+            lk.lock();
+        }
+    }
+    srv->exited = true;
+    srv->cv_done.notify_all();
+}
+
+extern "C" bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, bf_server *out) {
+    if (!out || !cfg) return bf_fail(plan, BF_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cfg->n_slots < 1 || cfg->n_slots > 8 || cfg->max_batch_jobs < 1 || cfg->queue_capacity < 1 ||
+        cfg->hbm_budget_bytes <= 0 || cfg->fake_device_us < 0)
+        return bf_fail(plan, BF_EINVAL, "bad serving configuration");
+    if (!plan && cfg->fake_device_us == 0) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    bf_server s = new bf_server_s();
+    s->plan = plan;
+    s->cfg = *cfg;
+    s->fake = cfg->fake_device_us > 0;
+    s->slots.resize(cfg->n_slots);
+    if (!s->fake) {
+        bf_status st = plan_ensure_device(plan);
+        if (st != BF_OK) {
+            delete s;
+            return st;
+        }
+        bool ok = cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&s->prep_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (Slot &sl : s->slots)
+            ok = ok && cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            for (Slot &sl : s->slots) {
+                if (sl.st) cudaStreamDestroy(sl.st);
+                if (sl.ev) cudaEventDestroy(sl.ev);
+            }
+            if (s->prep_st) cudaStreamDestroy(s->prep_st);
+            if (s->prep_ev) cudaEventDestroy(s->prep_ev);
+            delete s;
+            return bf_fail(plan, BF_ECUDA, "stream/event creation failed");
+        }
+    }
+    s->th = std::thread(dispatcher, s);
+    *out = s;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_serve_destroy(bf_server srv, int64_t timeout_us) {
+    if (!srv) return BF_OK;
+    {
+        std::unique_lock<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max<int64_t>(0, timeout_us));
+        if (!srv->cv_done.wait_until(lk, deadline, [&] { return srv->exited; })) {
+            srv->stop = false;  // keep serving; the caller may resume and retry
+            return bf_fail(srv->plan, BF_EBUSY, "server still has queued or running jobs");
+        }
+    }
+    srv->th.join();
+    if (!srv->fake) {
+        for (Slot &sl : srv->slots) {
+            cudaStreamSynchronize(sl.st);
+            cudaStreamDestroy(sl.st);
+            cudaEventDestroy(sl.ev);
+        }
+        cudaStreamSynchronize(srv->prep_st);
+        cudaStreamDestroy(srv->prep_st);
+        cudaEventDestroy(srv->prep_ev);
+        cudaGetLastError();
+    }
+    delete srv;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_serve_set_precoders(bf_server srv, const void *W_dev, const int32_t *f_host, int32_t n_prec,
+                                            int32_t first_id) {
+    if (!srv) return bf_fail(nullptr, BF_EINVAL, "server is NULL");
+    if (srv->fake) return BF_OK;
+    std::lock_guard<std::mutex> pl(srv->plan_mu);
+    bf_status s = bf_set_precoders(srv->plan, W_dev, f_host, n_prec, first_id, srv->prep_st);
+    if (s != BF_OK) return s;
+    if (cudaEventRecord(srv->prep_ev, srv->prep_st) != cudaSuccess)
+        return bf_fail(srv->plan, BF_ECUDA, "cudaEventRecord failed");
+    srv->prep_used = true;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticket) {
+    if (!srv || !job || !ticket) return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "NULL argument");
+    if (job->n_groups < 0 || (job->n_groups && !job->groups)) return bf_fail(srv->plan, BF_EINVAL, "bad groups");
+    if (job->prec < BF_FP32 || job->prec > BF_BF16X3) return bf_fail(srv->plan, BF_EINVAL, "bad precision");
+    if (job->n_groups && (!job->S_dev || !job->R_dev || ((uintptr_t)job->S_dev & 15) || ((uintptr_t)job->R_dev & 15)))
+        return bf_fail(srv->plan, BF_EINVAL, "S_dev and R_dev must be non-NULL and 16-byte aligned");
+    JobRec rec;
+    {
+        std::lock_guard<std::mutex> pl(srv->plan_mu);
+        const int *f_slot = srv->fake ? nullptr : srv->plan->f_slot.data();
+        for (int g = 0; g < job->n_groups; ++g) {
+            const bf_group &gr = job->groups[g];
+            if (gr.n_blocks < 0 || gr.s_off < 0 || gr.r_off < 0 || (gr.s_off & 15) || (gr.r_off & 15))
+                return bf_fail(srv->plan, BF_EINVAL, "group %d: bad block count or offsets", g);
+            if (!srv->fake && (gr.prec_id < 0 || gr.prec_id >= srv->plan->cap || f_slot[gr.prec_id] < 0))
+                return bf_fail(srv->plan, BF_ENOTFOUND, "group %d: precoder slot %d is not set", g, gr.prec_id);
+            bf_group a = gr;
+            a.s_off += (int64_t)(uintptr_t)job->S_dev;
+            a.r_off += (int64_t)(uintptr_t)job->R_dev;
+            rec.groups.push_back(a);
+        }
+        rec.bytes = srv->fake ? 0 : job_bytes(f_slot, job);
+        if (srv->fake)
+            for (int g = 0; g < job->n_groups; ++g)
+                rec.bytes += (int64_t)job->groups[g].n_blocks * (int64_t)R_BLOCK_BYTES;
+    }
+    rec.cell = job->cell;
+    rec.prec = job->prec;
+    rec.arrival_ns = job->arrival_ns ? job->arrival_ns : bf_now_ns();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (rec.bytes > srv->cfg.hbm_budget_bytes) {
+        srv->stats.rejected_budget++;
+        return bf_fail(srv->plan, BF_EBUDGET, "job needs %lld bytes, budget is %lld", (long long)rec.bytes,
+                       (long long)srv->cfg.hbm_budget_bytes);
+    }
+    if ((int)srv->queue.size() >= srv->cfg.queue_capacity) {
+        srv->stats.rejected_full++;
+        return bf_fail(srv->plan, BF_EAGAIN, "queue full (%d jobs)", srv->cfg.queue_capacity);
+    }
+    const uint64_t t = srv->next_ticket++;
+    srv->jobs.emplace(t, std::move(rec));
+    srv->queue.push_back(t);
+    srv->stats.submitted++;
+    *ticket = t;
+    srv->cv_work.notify_one();
+    return BF_OK;
+}
+
+static bf_status retire(bf_server srv, std::unordered_map<uint64_t, JobRec>::iterator it, double *latency_us) {
+    if (latency_us) *latency_us = (it->second.done_ns - it->second.arrival_ns) * 1e-3;
+    const bf_status st = it->second.status;
+    srv->jobs.erase(it);
+    return st;
+}
+
+extern "C" bf_status bf_poll(bf_server srv, uint64_t ticket, int *done, double *latency_us) {
+    if (!srv || !done) return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return bf_fail(srv->plan, BF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    *done = it->second.state == DONE;
+    if (!*done) return BF_OK;
+    return retire(srv, it, latency_us);
+}
+
+extern "C" bf_status bf_wait(bf_server srv, uint64_t ticket, int64_t timeout_us, double *latency_us) {
+    if (!srv) return bf_fail(nullptr, BF_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return bf_fail(srv->plan, BF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max<int64_t>(0, timeout_us));
+    const bool ok = srv->cv_done.wait_until(lk, deadline, [&] {
+        auto i = srv->jobs.find(ticket);
+        return i != srv->jobs.end() && i->second.state == DONE;
+    });
+    if (!ok) return bf_fail(srv->plan, BF_ETIMEOUT, "job %llu not done after %lld us", (unsigned long long)ticket,
+                            (long long)timeout_us);
+    return retire(srv, srv->jobs.find(ticket), latency_us);
+}
+
+extern "C" bf_status bf_serve_pause(bf_server srv, int32_t paused) {
+    if (!srv) return bf_fail(nullptr, BF_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->paused = paused != 0;
+    srv->cv_work.notify_all();
+    return BF_OK;
+}
+
+extern "C" bf_status bf_serve_get_stats(bf_server srv, bf_serve_stats *out) {
+    if (!srv || !out) return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->stats;
+    return BF_OK;
+}

@@ -1,0 +1,176 @@
+"""Host logic of the serving loop, on the CPU: the server runs with a fake
+device (every launch 'runs' for a fixed time on a host timer, no CUDA call),
+so admission, the HBM budget, batching, slots and the failure paths (stalled
+producer, full queue, oversized job, timeouts, unknown tickets, destroying a
+busy server) are exercised without a GPU."""
+import threading
+import time
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def bf():
+    from paper_1810_11451_gb300 import build
+    build.build()
+    import paper_1810_11451_gb300 as m
+    m.lib()
+    return m
+
+
+FAKE_S, FAKE_R = 0x100000, 0x200000
+R_BLOCK = 30720
+
+
+def job_groups(n_blocks):
+    return [(0, n_blocks, 0, 0)]
+
+
+def test_jobs_complete_in_order_with_latency(bf):
+    srv = bf.bf_serve_create(None, n_slots=1, max_batch_jobs=1, hbm_budget_bytes=1 << 30, fake_device_us=300)
+    try:
+        t0 = bf.bf_now_ns()
+        tickets = [bf.bf_submit(srv, job_groups(2), bf.BF_FP32, FAKE_S, FAKE_R, cell=i) for i in range(5)]
+        lats = [bf.bf_wait(srv, t, 5_000_000) for t in tickets]
+        assert all(l >= 300 for l in lats)
+        assert lats == sorted(lats)  # one slot, FIFO: later jobs wait longer
+        assert lats[-1] >= 5 * 300
+        st = bf.bf_serve_get_stats(srv)
+        assert st["submitted"] == 5 and st["completed"] == 5 and st["launches"] == 5
+        assert bf.bf_now_ns() - t0 >= 5 * 300_000
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_budget_limits_inflight_bytes(bf):
+    per_job = 3 * R_BLOCK
+    srv = bf.bf_serve_create(None, n_slots=4, max_batch_jobs=1, hbm_budget_bytes=2 * per_job, fake_device_us=500)
+    try:
+        ts = [bf.bf_submit(srv, job_groups(3), bf.BF_FP32, FAKE_S, FAKE_R) for _ in range(8)]
+        for t in ts:
+            bf.bf_wait(srv, t, 10_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["max_inflight_bytes"] <= 2 * per_job
+        assert st["max_busy_slots"] <= 2
+        assert st["budget_waits"] >= 1
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_submit(srv, job_groups(3 * 3), bf.BF_FP32, FAKE_S, FAKE_R)
+        assert ei.value.status == bf.BF_EBUDGET
+        assert bf.bf_serve_get_stats(srv)["rejected_budget"] == 1
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_continuous_batching_merges_and_overlaps(bf):
+    srv = bf.bf_serve_create(None, n_slots=2, max_batch_jobs=8, hbm_budget_bytes=1 << 34, fake_device_us=2000)
+    try:
+        first = bf.bf_submit(srv, job_groups(1), bf.BF_BF16X3, FAKE_S, FAKE_R)
+        time.sleep(0.0005)
+        # these arrive while the first launch runs: they start at once on the
+        # second slot, merged into one launch
+        rest = [bf.bf_submit(srv, job_groups(1), bf.BF_BF16X3, FAKE_S, FAKE_R) for _ in range(6)]
+        for t in [first] + rest:
+            bf.bf_wait(srv, t, 10_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["max_jobs_per_launch"] >= 2
+        assert st["max_busy_slots"] == 2
+        assert st["launches"] < 7
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_precisions_are_not_merged(bf):
+    srv = bf.bf_serve_create(None, n_slots=1, max_batch_jobs=8, hbm_budget_bytes=1 << 34, fake_device_us=1000)
+    try:
+        bf.bf_serve_pause(srv, True)
+        ts = [bf.bf_submit(srv, job_groups(1), p, FAKE_S, FAKE_R) for p in
+              (bf.BF_FP32, bf.BF_FP32, bf.BF_BF16X3, bf.BF_FP32)]
+        bf.bf_serve_pause(srv, False)
+        for t in ts:
+            bf.bf_wait(srv, t, 10_000_000)
+        assert bf.bf_serve_get_stats(srv)["launches"] == 3
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_stalled_producer_times_out_then_recovers(bf):
+    srv = bf.bf_serve_create(None, n_slots=1, hbm_budget_bytes=1 << 30, fake_device_us=100)
+    try:
+        bf.bf_serve_pause(srv, True)
+        t = bf.bf_submit(srv, job_groups(1), bf.BF_FP32, FAKE_S, FAKE_R)
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_wait(srv, t, 20_000)
+        assert ei.value.status == bf.BF_ETIMEOUT
+        done, _ = bf.bf_poll(srv, t)
+        assert not done
+        # destroying with queued work held back is refused, the server keeps going
+        with pytest.raises(bf.BfError):
+            bf.bf_serve_destroy(srv, 20_000)
+        bf.bf_serve_pause(srv, False)
+        assert bf.bf_wait(srv, t, 5_000_000) >= 20_000
+    finally:
+        bf.bf_serve_pause(srv, False)
+        bf.bf_serve_destroy(srv)
+
+
+def test_queue_full_and_unknown_tickets(bf):
+    srv = bf.bf_serve_create(None, n_slots=1, queue_capacity=3, hbm_budget_bytes=1 << 30, fake_device_us=100)
+    try:
+        bf.bf_serve_pause(srv, True)
+        ts = [bf.bf_submit(srv, job_groups(1), bf.BF_FP32, FAKE_S, FAKE_R) for _ in range(3)]
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_submit(srv, job_groups(1), bf.BF_FP32, FAKE_S, FAKE_R)
+        assert ei.value.status == bf.BF_EAGAIN
+        bf.bf_serve_pause(srv, False)
+        for t in ts:
+            bf.bf_wait(srv, t, 5_000_000)
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_poll(srv, ts[0])  # retired
+        assert ei.value.status == bf.BF_ENOTFOUND
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_poll(srv, 987654)
+        assert ei.value.status == bf.BF_ENOTFOUND
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_bad_arguments(bf):
+    with pytest.raises(bf.BfError):
+        bf.bf_serve_create(None, n_slots=0, fake_device_us=10)
+    with pytest.raises(bf.BfError):
+        bf.bf_serve_create(None, n_slots=2)  # real device needs a plan
+    srv = bf.bf_serve_create(None, n_slots=1, fake_device_us=10)
+    try:
+        for S, R, g in [(FAKE_S + 8, FAKE_R, job_groups(1)), (0, FAKE_R, job_groups(1)),
+                        (FAKE_S, FAKE_R, [(0, 1, 8, 0)]), (FAKE_S, FAKE_R, [(0, -1, 0, 0)])]:
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_submit(srv, g, bf.BF_FP32, S, R)
+            assert ei.value.status == bf.BF_EINVAL
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_concurrent_submitters(bf):
+    srv = bf.bf_serve_create(None, n_slots=3, max_batch_jobs=4, hbm_budget_bytes=1 << 34, fake_device_us=200)
+    tickets, lock = [], threading.Lock()
+
+    def cell(c):
+        for _ in range(25):
+            t = bf.bf_submit(srv, job_groups(1 + c % 3), bf.BF_FP32, FAKE_S, FAKE_R, cell=c)
+            with lock:
+                tickets.append(t)
+            time.sleep(0.0002)
+
+    th = [threading.Thread(target=cell, args=(c,)) for c in range(4)]
+    try:
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert len(set(tickets)) == 100
+        for t in tickets:
+            bf.bf_wait(srv, t, 10_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["completed"] == 100 and st["submitted"] == 100
+    finally:
+        bf.bf_serve_destroy(srv)
