@@ -1,0 +1,127 @@
+"""The serving loop on the GPU: per-TTI jobs from several cells, admitted under
+an HBM budget, merged and overlapped on the device. Each job's R equals its R
+computed alone, bit for bit, and matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1810_11451_gb300 as bf  # noqa: E402
+from bfrun import to_device_c64  # noqa: E402
+
+N_SYM = 14
+MAX_RB = 40
+
+
+class Cell:
+    """One cell: a bank of MAX_RB precoders (64 x f) and a resident S pool."""
+
+    def __init__(self, srv, cell, f, slot_base, seed):
+        rng = np.random.default_rng(seed)
+        self.cell, self.f, self.slot_base = cell, f, slot_base
+        self.W = [wl.precoder_unit_columns(rng, 64, f).astype(np.complex64) for _ in range(MAX_RB)]
+        self.S = wl.qam_symbols(rng, 64, (MAX_RB, N_SYM, f, 60)).astype(np.complex64)
+        self.Wd = to_device_c64(np.concatenate([w.ravel() for w in self.W]), torch)
+        self.Sd = to_device_c64(self.S.ravel(), torch)
+        torch.cuda.synchronize()  # the server's streams do not wait for torch's stream
+        bf.bf_serve_set_precoders(srv, self.Wd, [f] * MAX_RB, slot_base)
+
+    def groups(self, n_rb):
+        blk_s = N_SYM * self.f * 480
+        return [(self.slot_base + rb, N_SYM, rb * blk_s, rb * N_SYM * 30720) for rb in range(n_rb)]
+
+    def new_R(self, n_rb):
+        return torch.full((n_rb * N_SYM * 64 * 60 * 2,), float("nan"), device="cuda")
+
+    def reference(self, n_rb):
+        return [oracle.apply_blocks(self.W[rb], self.S[rb]) for rb in range(n_rb)]
+
+
+def _R_np(Rt, n_rb):
+    torch.cuda.synchronize()
+    return Rt.cpu().numpy().view(np.complex64).reshape(n_rb, N_SYM, 64, 60)
+
+
+@pytest.fixture(scope="module")
+def plan():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    p = bf.bf_plan_create(64, 36, 60)
+    yield p
+    bf.bf_plan_destroy(p)
+
+
+@pytest.mark.parametrize("prec,tol", [(bf.BF_FP32, 1e-5), (bf.BF_BF16X3, 1e-5)], ids=["fp32", "bf16x3"])
+def test_alone_equals_in_mix(plan, prec, tol):
+    srv = bf.bf_serve_create(plan, n_slots=4, max_batch_jobs=8, hbm_budget_bytes=8 << 30)
+    try:
+        cells = [Cell(srv, c, f, 1000 + 100 * c, 50 + c) for c, f in enumerate([36, 9, 17, 1])]
+        torch.cuda.synchronize()
+        probe = cells[0]
+        R_alone = probe.new_R(25)
+        torch.cuda.synchronize()
+        lat = bf.bf_wait(srv, bf.bf_submit(srv, probe.groups(25), prec, probe.Sd, R_alone), 10_000_000)
+        assert 0 < lat < 1e6
+        alone = _R_np(R_alone, 25)
+        # the mix: 32 jobs of uneven size from 4 cells, submitted back to back
+        rng = np.random.default_rng(7)
+        spec = []
+        for k in range(32):
+            c, n_rb = cells[k % 4], int(rng.integers(1, MAX_RB + 1))
+            if k == 12:
+                c, n_rb = probe, 25
+            spec.append((c, n_rb, c.new_R(n_rb)))
+        torch.cuda.synchronize()
+        jobs = [(c, n_rb, Rt, bf.bf_submit(srv, c.groups(n_rb), prec, c.Sd, Rt, cell=c.cell))
+                for c, n_rb, Rt in spec]
+        lats = [bf.bf_wait(srv, t, 20_000_000) for (_, _, _, t) in jobs]
+        st = bf.bf_serve_get_stats(srv)
+        assert st["completed"] == 33 and st["max_busy_slots"] >= 2, st
+        mixed = _R_np(jobs[12][2], 25)
+        assert np.array_equal(mixed.view(np.uint64), alone.view(np.uint64)), "job differs alone vs in the mix"
+        for c, n_rb, Rt, _ in jobs[:8]:
+            R = _R_np(Rt, n_rb)
+            e = oracle.rel_frobenius(list(R), c.reference(n_rb))
+            assert e <= tol, e
+        assert max(lats) < 1e6
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_budget_serialises_and_precoder_update_is_ordered(plan):
+    c_bytes = 10 * N_SYM * (36 * 480 + 30720)
+    srv = bf.bf_serve_create(plan, n_slots=4, max_batch_jobs=4, hbm_budget_bytes=int(1.5 * c_bytes))
+    try:
+        cell = Cell(srv, 0, 36, 5000, 91)
+        Rs = [cell.new_R(10) for _ in range(6)]
+        torch.cuda.synchronize()
+        ts = [bf.bf_submit(srv, cell.groups(10), bf.BF_BF16X3, cell.Sd, R) for R in Rs]
+        for t in ts:
+            bf.bf_wait(srv, t, 20_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["max_inflight_bytes"] <= 1.5 * c_bytes and st["budget_waits"] >= 1, st
+        ref = cell.reference(10)
+        for R in Rs:
+            assert oracle.rel_frobenius(list(_R_np(R, 10)), ref) <= 1e-5
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_submit(srv, cell.groups(20), bf.BF_BF16X3, cell.Sd, Rs[0])
+        assert ei.value.status == bf.BF_EBUDGET
+        # new precoders for the same slots: jobs submitted afterwards use them
+        rng = np.random.default_rng(3)
+        cell.W = [wl.precoder_unit_columns(rng, 64, 36).astype(np.complex64) for _ in range(MAX_RB)]
+        Wd2 = to_device_c64(np.concatenate([w.ravel() for w in cell.W]), torch)
+        R2 = cell.new_R(10)
+        torch.cuda.synchronize()
+        bf.bf_serve_set_precoders(srv, Wd2, [36] * MAX_RB, cell.slot_base)
+        bf.bf_wait(srv, bf.bf_submit(srv, cell.groups(10), bf.BF_BF16X3, cell.Sd, R2), 20_000_000)
+        assert oracle.rel_frobenius(list(_R_np(R2, 10)), cell.reference(10)) <= 1e-5
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_submit(srv, [(99999, 1, 0, 0)], bf.BF_FP32, cell.Sd, R2)
+        assert ei.value.status == bf.BF_ENOTFOUND
+    finally:
+        bf.bf_serve_destroy(srv)
