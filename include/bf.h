@@ -226,6 +226,26 @@ int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *g
 bf_status bf_errnorm(bf_plan plan, const void *R_dev, const void *Rref_dev, int64_t n_blocks,
                      double *per_block_dev, double *total_host, void *stream);
 
+/* The same accuracy report for callers that cannot allocate device memory
+ * (the paper has no counterpart; it is a library convenience). A per-TTI
+ * real-time loop must not call cudaMalloc or cudaFree, which may synchronise
+ * the device and take unbounded time, and some callers run where another
+ * allocator owns all device memory or have no plan. This call takes no plan
+ * and allocates nothing: its scratch is a fixed device array inside the
+ * library, 2 doubles per block for at most BF_ERRNORM_NOALLOC_MAX_BLOCKS
+ * blocks (about 1 MiB), which every GPU that loads the library keeps until
+ * the process exits.
+ *  R_dev, Rref_dev, n_blocks, total_host : as bf_errnorm (no per-block output).
+ * n_blocks above the maximum gives BF_EINVAL (text in bf_last_error(NULL)).
+ * The first call on a device looks the array's device address up for that
+ * device (the current one); make that first call before any stream capture.
+ * All calls share the one array: calls whose kernels overlap on the GPU (on
+ * different streams or host threads) race and may return wrong totals, so
+ * order them. Synchronises `stream`. */
+#define BF_ERRNORM_NOALLOC_MAX_BLOCKS 65536
+bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev, int64_t n_blocks,
+                             double *total_host, void *stream);
+
 /* Number of product kernels (or graph replays) this plan has launched so far
  * (0 for a NULL plan). */
 int64_t bf_plan_launch_count(bf_plan plan);

@@ -215,6 +215,22 @@ def bf_plan_launch_count(plan) -> int:
     return int(lib().bf_plan_launch_count(plan))
 
 
+BF_ERRNORM_NOALLOC_MAX_BLOCKS = 65536
+
+
+def bf_errnorm_noalloc(R_dev, Rref_dev, n_blocks: int, stream=None) -> Tuple[float, float]:
+    """bf_errnorm without a plan and without any device allocation (fixed
+    in-library scratch, at most BF_ERRNORM_NOALLOC_MAX_BLOCKS blocks)."""
+    L = lib()
+    L.bf_errnorm_noalloc.restype = c_int
+    L.bf_errnorm_noalloc.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_double), c_void_p]
+    tot = (c_double * 2)()
+    st = L.bf_errnorm_noalloc(_ptr(R_dev), _ptr(Rref_dev), int(n_blocks), tot, _stream(stream))
+    if st != BF_OK:
+        raise BfError(st, bf_last_error(None))
+    return float(tot[0]), float(tot[1])
+
+
 # ---------------------------------------------------------------- serving (bf_serve.h)
 class bf_serve_config(ctypes.Structure):
     _fields_ = [("n_slots", c_int32), ("max_batch_jobs", c_int32), ("queue_capacity", c_int32),

@@ -1,0 +1,83 @@
+// bf_noalloc.cu -- bf_errnorm_noalloc: the accuracy report of bf_errnorm for
+// callers that cannot allocate device memory.
+//
+// Who needs it: a per-TTI real-time loop (one slot every 0.5 ms) must not call
+// cudaMalloc or cudaFree, which can synchronise the whole device and take an
+// unbounded time; neither can code running where another allocator owns all of
+// the process's device memory, or code that has no plan at hand. This entry
+// point needs no plan and allocates nothing: its scratch (the per-block
+// partial sums and the two totals) is a file-scope device array of fixed size,
+// which every GPU that loads the library holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "bf.h"
+#include "bf_plan.h"
+#include "bf_prep.h"
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+
+// Scratch shared by every call: 2 doubles per block, then the 2 totals.
+static __device__ __align__(256) double g_errnorm_scratch[2 * BF_ERRNORM_NOALLOC_MAX_BLOCKS + 2];
+
+// Per-device set-up: the scratch array's device address (in host code the
+// symbol is only a host-side stand-in) and the SM count for the grid.
+struct DevState {
+    bool ready = false;
+    double *scratch = nullptr;
+    int sms = 0;
+};
+DevState g_dev[MAX_DEVICES];
+std::mutex g_mu;
+
+}  // namespace
+
+extern "C" bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev, int64_t n_blocks,
+                                        double *total_host, void *stream) {
+    if (!total_host) return bf_fail(nullptr, BF_EINVAL, "total_host is NULL");
+    if (n_blocks < 0 || n_blocks > BF_ERRNORM_NOALLOC_MAX_BLOCKS)
+        return bf_fail(nullptr, BF_EINVAL, "n_blocks = %lld is outside [0, %d], the size of the fixed scratch",
+                       (long long)n_blocks, BF_ERRNORM_NOALLOC_MAX_BLOCKS);
+    if (n_blocks > 0 && (!R_dev || !Rref_dev)) return bf_fail(nullptr, BF_EINVAL, "NULL R_dev or Rref_dev");
+    if (((uintptr_t)R_dev & 15u) || ((uintptr_t)Rref_dev & 15u))
+        return bf_fail(nullptr, BF_EINVAL, "R_dev and Rref_dev must be 16-byte aligned");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= MAX_DEVICES) return bf_fail(nullptr, BF_ECUDA, "device ordinal %d out of range", dev);
+    DevState st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_dev[dev].ready) {
+            // First call on this device, which is current: look the array's
+            // device address up once. Make this first call before any capture.
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_errnorm_scratch);
+            if (e != cudaSuccess)
+                return bf_fail(nullptr, BF_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            int sms = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess)
+                return bf_fail(nullptr, BF_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+            g_dev[dev].scratch = static_cast<double *>(p);
+            g_dev[dev].sms = sms;
+            g_dev[dev].ready = true;
+        }
+        st = g_dev[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // Nothing needs clearing: the kernels write every per-block pair they later
+    // read, and the totals, before anything reads them.
+    double *per_block = st.scratch;
+    double *total = st.scratch + 2 * BF_ERRNORM_NOALLOC_MAX_BLOCKS;
+    e = bfi::launch_errnorm((const float2 *)R_dev, (const double2 *)Rref_dev, n_blocks, per_block, total,
+                            st.sms * 8, s);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "error-norm launch: %s", cudaGetErrorString(e));
+    e = cudaMemcpyAsync(total_host, total, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "copying the totals: %s", cudaGetErrorString(e));
+    return BF_OK;
+}
