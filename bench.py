@@ -170,6 +170,23 @@ def cpu_baseline(batch, budget_s: float = 12.0):
             "sample": f"the whole workload ({batch.total_blocks} blocks) x {reps} repetitions, {dt:.1f} s, FP64"}, ref
 
 
+def cpu_references(done, batches):
+    """Part of the CPU-baseline leg: the oracle's R for the other workloads
+    (complex64 inputs widened to FP64), flattened in group order."""
+    import oracle
+    out = {k: np.concatenate([r.reshape(-1) for r in v]) for k, v in done.items()}
+    for name, b in batches.items():
+        if b is not None:
+            out[name] = np.concatenate([r.reshape(-1) for r in oracle.apply_batch(b.rounded(np.complex64))])
+    return out
+
+
+def to_device_ref(torch, ref):
+    if ref is None:
+        return None
+    return torch.from_numpy(np.ascontiguousarray(ref).view(np.float64)).cuda()
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores on this workload."""
     dist, rank, world = dist_init()
@@ -243,16 +260,123 @@ def end_to_end(torch, bf, plan, Sflat, lay, r_numel, stream, dist, world, flops,
             "h2d_bytes_per_step": int(lay.s_bytes), "d2h_bytes_per_step": int(lay.r_blocks * 30720)}
 
 
+def graph_rate(torch, bf, handle, steps, stream):
+    """Median launch time (ms) of one prepared batch, CUDA events per launch."""
+    _, per = time_graphs(torch, bf, [handle], steps, 5, stream)
+    return statistics.median(per)
+
+
+def rel_err(torch, bf, plan, R_t, ref_d, n_blocks, stream):
+    if ref_d is None:
+        return None
+    num, den = bf.bf_errnorm(plan, R_t, ref_d, n_blocks, None, stream)
+    return float(np.sqrt(num / den)) if den > 0 else 0.0
+
+
+def uneven_leg(torch, bf, plan, batch, ref_d, stream, steps=200):
+    """Uneven batch (16,384 blocks, f ~ U{0..36} per group, geometric groups):
+    one persistent graph-captured launch, before and after the autotuner."""
+    from bfrun import layout, set_precoders, to_device_c64
+    set_precoders(plan, batch, torch)
+    lay = layout(batch)
+    Sflat, _ = batch.pack_S()
+    S = to_device_c64(Sflat, torch)
+    R = torch.empty(lay.r_blocks * 64 * 60 * 2, dtype=torch.float32, device="cuda")
+    out = {"blocks": batch.total_blocks, "groups": batch.n_groups, "gflop": batch.flops() / 1e9,
+           "algorithmic_bytes": batch.algorithmic_bytes()}
+    for phase in ("untuned", "tuned"):
+        if phase == "tuned":
+            t0 = time.perf_counter()
+            bf.bf_autotune(plan, bf.BF_BF16X3, stream)
+            bf.bf_autotune(plan, bf.BF_FP32, stream)
+            out["autotune_s"] = time.perf_counter() - t0
+            out["tune_table"] = {name: [bf.bf_tune_query(plan, p, f) for f in (0, 8, 16, 24, 36)]
+                                 for name, p in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32))}
+        for name, prec in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32)):
+            h = bf.bf_batch_create(plan, S, None, lay.groups, prec, R)
+            ms = graph_rate(torch, bf, h, steps, stream)
+            bf.bf_batch_launch(h, stream)
+            err = rel_err(torch, bf, plan, R, ref_d, lay.r_blocks, stream)
+            bf.bf_batch_destroy(h)
+            out[f"{name}_{phase}"] = {"kernel_ms": ms, "gflops": batch.flops() / ms / 1e6,
+                                      "blocks_per_s": batch.total_blocks / ms * 1e3,
+                                      "hbm_gbs": batch.algorithmic_bytes() / ms / 1e6, "rel_err": err}
+    return out
+
+
+def reduced_leg(torch, bf, plan, batch, ref_d, stream, steps=50):
+    """Reduced precision (full band x 8 = 30,576 blocks, 256-QAM + noise): held
+    bf16 / fp16 / split images (quantisation timed on its own) and split-bf16
+    on complex64."""
+    from bfrun import layout, set_precoders, to_device_c64
+    set_precoders(plan, batch, torch)
+    lay = layout(batch)
+    Sflat, _ = batch.pack_S()
+    S = to_device_c64(Sflat, torch)
+    del Sflat
+    R = torch.empty(lay.r_blocks * 64 * 60 * 2, dtype=torch.float32, device="cuda")
+    nb = batch.total_blocks
+    out = {"blocks": nb, "gflop": batch.flops() / 1e9}
+    for name, prec, held in (("bf16_held", bf.BF_BF16, True), ("fp16_held", bf.BF_FP16, True),
+                             ("bf16x3_held", bf.BF_BF16X3, True), ("bf16x3_c64", bf.BF_BF16X3, False)):
+        r = {}
+        if held:
+            lh = layout(batch, 0, prec)
+            Sq = torch.empty(lh.held_bytes // 4 + 4, dtype=torch.float32, device="cuda")
+            sc = torch.empty(nb, dtype=torch.float32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for i in range(6):
+                if i == 1:
+                    e0.record(stream)
+                bf.bf_quantize_symbols(plan, S, lay.groups, prec, Sq, lh.held_off, sc, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            qms = e0.elapsed_time(e1) / 5
+            r["quantize_ms"] = qms
+            r["quantize_gbs"] = (lay.s_bytes + lh.held_bytes) / qms / 1e6
+            groups = [(g[0], g[1], lh.held_off[i], g[3]) for i, g in enumerate(lay.groups)]
+            h = bf.bf_batch_create(plan, Sq, sc, groups, prec, R)
+            s_bytes = lh.held_bytes
+        else:
+            h = bf.bf_batch_create(plan, S, None, lay.groups, prec, R)
+            s_bytes = lay.s_bytes
+        ms = graph_rate(torch, bf, h, steps, stream)
+        bf.bf_batch_launch(h, stream)
+        r.update({"kernel_ms": ms, "gflops": batch.flops() / ms / 1e6, "blocks_per_s": nb / ms * 1e3,
+                  "moved_gbs": (s_bytes + nb * 30720 + len(batch.W) * 64 * 36 * 8) / ms / 1e6,
+                  "rel_err": rel_err(torch, bf, plan, R, ref_d, nb, stream)})
+        bf.bf_batch_destroy(h)
+        if held:
+            del Sq, sc
+        out[name] = r
+    return out
+
+
+def serving_leg(torch, bf, ttis, prec):
+    """Continuous-batching serving of 8 cells in real time (0.5 ms TTIs)."""
+    import workloads as wl
+    from serving_sim import ServingSim
+    plan = bf.bf_plan_create(64, 36, 60)
+    sim = ServingSim(plan, torch, prec=prec)
+    try:
+        return sim.run(wl.serving_schedule(n_tti=ttis))
+    finally:
+        sim.close()
+        bf.bf_plan_destroy(plan)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain leg")
     ap.add_argument("--sets", type=int, default=3, help="rotating buffer sets (3 keeps the working set above L2)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven, reduced-precision and serving legs")
+    ap.add_argument("--serving-ttis", type=int, default=20000, help="TTIs of the split-bf16 serving run")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -308,19 +432,41 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(torch, bf, plan, Sflat, lay, R_sets[0].numel(), stream, dist, world, flops)
 
-    # ---- CPU baseline (oracle) and the accuracy of the timed output
-    cpu, acc = None, None
+    # ---- CPU baseline (oracle), which also gives the references for accuracy
+    cpu, acc, refs = None, None, {}
+    extra = not args.no_extra and rank == 0
+    b_uneven = wl.config_uneven() if extra else None
+    b_reduced = wl.config_reduced() if extra else None
     if rank == 0 and not args.no_cpu:
         cpu, ref = cpu_baseline(batch)
-        Rref = np.concatenate([r.reshape(-1) for r in ref])
-        Rref_d = torch.from_numpy(Rref.view(np.float64)).cuda()
+        refs = cpu_references({"fullband": ref}, {"uneven": b_uneven, "reduced": b_reduced})
+        Rref_d = to_device_ref(torch, refs.pop("fullband"))
+        acc = {}
         for name, h in (("bf16x3", best[0]), ("fp32", plain[0])):
             bf.bf_batch_launch(h, stream)
             num, den = bf.bf_errnorm(plan, R_sets[0], Rref_d, lay.r_blocks, None, stream)
-            acc = acc or {}
             acc[name] = float(np.sqrt(num / den))
+        del Rref_d
+    for s in range(n_sets):
+        bf.bf_batch_destroy(best[s])
+        bf.bf_batch_destroy(plain[s])
+    del S_sets, R_sets
+    torch.cuda.empty_cache()
+
+    # ---- the other workloads: uneven batching, reduced precision, serving
+    legs = {}
+    if extra:
+        ref_d = to_device_ref(torch, refs.pop("uneven", None))
+        legs["uneven"] = uneven_leg(torch, bf, plan, b_uneven, ref_d, stream)
+        del ref_d
+        ref_d = to_device_ref(torch, refs.pop("reduced", None))
+        legs["reduced"] = reduced_leg(torch, bf, plan, b_reduced, ref_d, stream)
+        del ref_d
+        torch.cuda.empty_cache()
+        legs["serving_bf16x3"] = serving_leg(torch, bf, args.serving_ttis, bf.BF_BF16X3)
+        legs["serving_fp32"] = serving_leg(torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
     status = bf.bf_device_status(plan)
-    
+
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     line = {
@@ -346,9 +492,10 @@ def main():
         "gpu_launches": int(launches),
         "device_status": bf.bf_status_string(status),
     }
-    for s in range(n_sets):
-        bf.bf_batch_destroy(best[s])
-        bf.bf_batch_destroy(plain[s])
+    if legs:
+        srv = legs.get("serving_bf16x3", {})
+        line["p99_tti_latency_ms"] = srv.get("p99_us", float("nan")) / 1e3 if srv else None
+        line["legs"] = legs
     bf.bf_plan_destroy(plan)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -214,6 +214,31 @@ int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *g
                     bf_precision prec, int32_t held, int32_t max_cta, bf_tile *tiles_out,
                     int32_t max_tiles, int32_t *cta_begin_out, int32_t *n_cta_out);
 
+/* ------------------------------------------------------------------ autotuner */
+
+/* Tune `prec` on this GPU, the way the paper's optimizer picks the best
+ * building block per size and target (Sec. IV). For each f bucket ([0],
+ * [1,8], [9,16], [17,24], [25,36], measured at f = 0, 8, 16, 24, 36) it times
+ * synthetic complex64 batches of sm_count*8 and sm_count*32 blocks, 14 blocks
+ * per precoder, with tiles of 1 and of 2 blocks. It keeps the faster tile size
+ * and records the marginal cost per block (the slope in ns). Later batches of
+ * this precision are cut with those tile sizes and split across CTAs by those
+ * costs instead of by bytes. For BF_FP32 it also picks 1 or 2 CTAs per SM.
+ * Allocates and frees its own scratch (about 240 MB) and runs on `stream`
+ * (synchronised before return). Uses 80 precoder slots above the plan's
+ * current slots, which it leaves unset. */
+bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream);
+
+/* The table entry used for (prec, f): marginal ns per block, tile size,
+ * and whether prec has been tuned. Any output pointer may be NULL. */
+bf_status bf_tune_query(bf_plan plan, bf_precision prec, int32_t f, double *ns_per_block,
+                        int32_t *tile_blocks, int32_t *tuned);
+
+/* Write / read the plan's autotune table as JSON ("libbf-tune-1"). A table
+ * is only meaningful on the kind of GPU that measured it. */
+bf_status bf_tune_save(bf_plan plan, const char *path);
+bf_status bf_tune_load(bf_plan plan, const char *path);
+
 /* ------------------------------------------------------------------ accuracy report */
 
 /* Relative Frobenius error of R against a reference, accumulated in FP64.

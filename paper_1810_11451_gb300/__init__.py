@@ -215,6 +215,40 @@ def bf_plan_launch_count(plan) -> int:
     return int(lib().bf_plan_launch_count(plan))
 
 
+def _tune_sigs(L):
+    if not getattr(L, "_tune_sigs", False):
+        L.bf_autotune.restype = c_int
+        L.bf_autotune.argtypes = [c_void_p, c_int, c_void_p]
+        L.bf_tune_query.restype = c_int
+        L.bf_tune_query.argtypes = [c_void_p, c_int, c_int32, POINTER(c_double), POINTER(c_int32),
+                                    POINTER(c_int32)]
+        L.bf_tune_save.restype = c_int
+        L.bf_tune_save.argtypes = [c_void_p, c_char_p]
+        L.bf_tune_load.restype = c_int
+        L.bf_tune_load.argtypes = [c_void_p, c_char_p]
+        L._tune_sigs = True
+    return L
+
+
+def bf_autotune(plan, prec: int, stream=None) -> None:
+    _check(_tune_sigs(lib()).bf_autotune(plan, int(prec), _stream(stream)), plan)
+
+
+def bf_tune_query(plan, prec: int, f: int) -> dict:
+    ns, tb, tuned = c_double(), c_int32(), c_int32()
+    _check(_tune_sigs(lib()).bf_tune_query(plan, int(prec), int(f), ctypes.byref(ns), ctypes.byref(tb),
+                                           ctypes.byref(tuned)), plan)
+    return {"ns_per_block": ns.value, "tile_blocks": tb.value, "tuned": bool(tuned.value)}
+
+
+def bf_tune_save(plan, path: str) -> None:
+    _check(_tune_sigs(lib()).bf_tune_save(plan, path.encode()), plan)
+
+
+def bf_tune_load(plan, path: str) -> None:
+    _check(_tune_sigs(lib()).bf_tune_load(plan, path.encode()), plan)
+
+
 BF_ERRNORM_NOALLOC_MAX_BLOCKS = 65536
 
 

@@ -333,24 +333,34 @@ extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const 
 }
 
 // ------------------------------------------------------------------ work lists
-// Tiles of up to `tile_blocks` consecutive blocks of one group; the run of
-// tiles is split into n_cta contiguous ranges of about equal cost (bytes
-// moved, weighted per f by the autotune table), so each CTA loads a precoder
-// once per range and streams its S blocks.
+// Tiles of 1 or 2 consecutive blocks of one group (the tile size per f bucket
+// comes from the autotune table); the run of tiles is split into n_cta
+// contiguous ranges of about equal cost (measured ns per block once tuned,
+// bytes moved before), so each CTA loads a precoder once per range and
+// streams its S blocks.
 void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *groups, int32_t n_groups,
                     bf_precision prec, bool held, int max_cta, WorkList &wl) {
-    wl.tiles.clear();
-    wl.cta_begin.clear();
-    const int tile_blocks = 2;
-    std::vector<double> cost;
-    int blk = 0;
+    // count first, so the arrays are sized once (the buffers persist across
+    // calls in the plan, so steady-state scheduling allocates nothing)
+    int n_tiles = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        const int tb = tune.tile_blocks_for(prec, f_slot[groups[g].prec_id]);
+        n_tiles += (groups[g].n_blocks + tb - 1) / tb;
+    }
+    wl.tiles.resize(n_tiles);
+    wl.cost.resize(n_tiles);
+    Tile *tiles = wl.tiles.data();
+    double *cost = wl.cost.data();
+    double total = 0;
+    int blk = 0, n = 0;
     for (int g = 0; g < n_groups; ++g) {
         const bf_group &gr = groups[g];
         const int f = f_slot[gr.prec_id];
-        const int64_t sb = held ? bf_held_block_bytes(f, prec) : (int64_t)f * S_BYTES_PER_F;
-        const double w = tune.cost_weight(prec, f);
-        for (int b0 = 0; b0 < gr.n_blocks; b0 += tile_blocks) {
-            Tile t{};
+        const int64_t sb = held ? held_block_bytes(f, prec == BF_BF16X3 ? 2 : 1) : (int64_t)f * S_BYTES_PER_F;
+        const int tile_blocks = tune.tile_blocks_for(prec, f);
+        const double c1 = tune.cost(prec, f, 1, (double)(sb + R_BLOCK_BYTES));
+        for (int b0 = 0; b0 < gr.n_blocks; b0 += tile_blocks, ++n) {
+            Tile &t = tiles[n];
             t.s_off = gr.s_off + (int64_t)b0 * sb;
             t.r_off = gr.r_off + (int64_t)b0 * R_BLOCK_BYTES;
             t.prec = gr.prec_id;
@@ -358,23 +368,21 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
             t.f = (int16_t)f;
             t.nblk = (int16_t)std::min(tile_blocks, gr.n_blocks - b0);
             t.flags = 0;
-            wl.tiles.push_back(t);
-            cost.push_back(w * t.nblk * (double)(sb + R_BLOCK_BYTES));
+            cost[n] = c1 * t.nblk;
+            total += cost[n];
         }
         blk += gr.n_blocks;
     }
-    const int n_tiles = (int)wl.tiles.size();
     const int n_cta = std::max(1, std::min(max_cta, n_tiles));
-    double total = 0;
-    for (double c : cost) total += c;
     wl.cta_begin.assign(n_cta + 1, n_tiles);
     wl.cta_begin[0] = 0;
     // midpoint rule: tile t goes to CTA floor((cum + cost/2) / (total / n_cta)),
     // clamped so that ranges stay contiguous and no CTA is left empty
     double cum = 0;
     int cur = 0;
+    const double per_cost = total > 0 ? n_cta / total : 0.0;
     for (int t = 0; t < n_tiles; ++t) {
-        int c = total > 0 ? (int)((cum + 0.5 * cost[t]) * n_cta / total) : 0;
+        int c = (int)((cum + 0.5 * cost[t]) * per_cost);
         const int lo = std::max(cur, n_cta - (n_tiles - t));
         const int hi = std::min(t > 0 ? cur + 1 : 0, n_cta - 1);
         c = std::min(std::max(c, lo), hi);
@@ -387,16 +395,16 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
         int prev = -1;
         int last_idx = -1;
         for (int t = wl.cta_begin[c]; t < wl.cta_begin[c + 1]; ++t) {
-            Tile &tl = wl.tiles[t];
+            Tile &tl = tiles[t];
             if (tl.f == 0) continue;
             if (tl.prec != prev) {
                 tl.flags |= TF_FIRST_OF_W;
-                if (last_idx >= 0) wl.tiles[last_idx].flags |= TF_LAST_OF_W;
+                if (last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
             }
             prev = tl.prec;
             last_idx = t;
         }
-        if (last_idx >= 0) wl.tiles[last_idx].flags |= TF_LAST_OF_W;
+        if (last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
     }
 }
 
@@ -411,8 +419,8 @@ extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const 
         const int f = f_of_slot[groups[g].prec_id];
         if (f < 0 || f > F_LIMIT) return -BF_EINVAL;
     }
-    WorkList wl;
-    TuneTable tune;
+    static thread_local WorkList wl;  // reused: repeated calls allocate nothing
+    const TuneTable tune;
     build_worklist(f_of_slot, tune, groups, n_groups, prec, held != 0, max_cta, wl);
     const int nt = (int)wl.tiles.size();
     *n_cta_out = (int32_t)wl.cta_begin.size() - 1;

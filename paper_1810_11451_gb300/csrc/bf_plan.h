@@ -11,28 +11,39 @@
 
 namespace bfi {
 
-// Autotune table: per precision and f bucket, the measured cost of one block
-// relative to its byte count (weights the static split of uneven batches),
-// and the launch shape of the CUDA-core kernel.
+// Autotune table. Per precision and f bucket: the measured marginal cost of
+// one block (ns, the slope of launch time over batch size) and the tile
+// size (1 or 2 blocks) that measured faster. An untuned precision splits
+// batches by bytes moved instead. Also the CTAs per SM of the CUDA-core kernel.
 constexpr int TUNE_BUCKETS = 5;  // f in [0], [1,8], [9,16], [17,24], [25,36]
+constexpr int TUNE_REP_F[TUNE_BUCKETS] = {0, 8, 16, 24, 36};
 __host__ __device__ constexpr int f_bucket(int f) {
     return f <= 0 ? 0 : (f <= 8 ? 1 : (f <= 16 ? 2 : (f <= 24 ? 3 : 4)));
 }
 
 struct TuneTable {
-    double weight[4][TUNE_BUCKETS];  // [precision][bucket], 1.0 = cost proportional to bytes
+    double ns_per_block[4][TUNE_BUCKETS];
+    int tile_blocks[4][TUNE_BUCKETS];
+    bool tuned[4] = {false, false, false, false};
     int simt_ctas_per_sm = 2;
-    bool tuned = false;
     TuneTable() {
-        for (auto &row : weight)
-            for (double &w : row) w = 1.0;
+        for (int p = 0; p < 4; ++p)
+            for (int b = 0; b < TUNE_BUCKETS; ++b) {
+                ns_per_block[p][b] = 0.0;
+                tile_blocks[p][b] = 2;
+            }
     }
-    double cost_weight(int prec, int f) const { return weight[prec & 3][f_bucket(f)]; }
+    int tile_blocks_for(int prec, int f) const { return tile_blocks[prec & 3][f_bucket(f)]; }
+    // Scheduling cost of n blocks at f whose S and R take `bytes_per_block`.
+    double cost(int prec, int f, int n, double bytes_per_block) const {
+        return tuned[prec & 3] ? n * ns_per_block[prec & 3][f_bucket(f)] : n * bytes_per_block;
+    }
 };
 
 struct WorkList {
     std::vector<Tile> tiles;
     std::vector<int32_t> cta_begin;
+    std::vector<double> cost;  // scheduling cost per tile (scratch)
 };
 
 // One work-list buffer of the ring: pinned host image, device copy, and the

@@ -138,24 +138,35 @@ __global__ void __launch_bounds__(256) bf_quantize_kernel(const uint8_t *__restr
     constexpr int TERMS = FMT == 2 ? 2 : 1;
     uint8_t *dst = Sq + g.q_off + (int64_t)b * held_block_bytes(f, TERMS);
     const int term_bytes = 64 * kpad * 2;
-    // One complex value (two adjacent K columns) per thread step: 4-byte stores.
-    for (int e = threadIdx.x; e < 64 * (kpad / 2); e += blockDim.x) {
-        const int row = e / (kpad / 2), k = e - row * (kpad / 2);
-        float2 v = make_float2(0.f, 0.f);
-        if (row < B_RE && k < f) v = s[k * B_RE + row];
-        const float xr = v.x * inv, xi = v.y * inv;
-        const int off = tc_offset(row, 2 * k, kpad);
-        if (FMT == 1) {
-            *reinterpret_cast<__half2 *>(dst + off) = __floats2half2_rn(xr, xi);
-        } else {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(xr, xi);
-            *reinterpret_cast<__nv_bfloat162 *>(dst + off) = h;
-            if (FMT == 2) {
-                const float2 hb = __bfloat1622float2(h);
-                *reinterpret_cast<__nv_bfloat162 *>(dst + term_bytes + off) =
-                    __floats2bfloat162_rn(xr - hb.x, xi - hb.y);
+    // One task = one row (resource element j) and one 8-column chunk q (flows
+    // 4q..4q+3): consecutive threads take consecutive rows, so the reads of a
+    // warp cover 256 contiguous bytes of one flow row of S and its writes 16
+    // contiguous bytes per row, 128 per 8 rows.
+    for (int e = threadIdx.x; e < 64 * (kpad / 8); e += blockDim.x) {
+        const int q = e >> 6, row = e & 63;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * q + u;
+            float2 v = make_float2(0.f, 0.f);
+            if (row < B_RE && k < f) v = s[k * B_RE + row];
+            const float xr = v.x * inv, xi = v.y * inv;
+            if (FMT == 1) {
+                const __half2 h = __floats2half2_rn(xr, xi);
+                hi[u] = *reinterpret_cast<const uint32_t *>(&h);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(xr, xi);
+                hi[u] = *reinterpret_cast<const uint32_t *>(&h);
+                if (FMT == 2) {
+                    const float2 hb = __bfloat1622float2(h);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(xr - hb.x, xi - hb.y);
+                    lo[u] = *reinterpret_cast<const uint32_t *>(&l);
+                }
             }
         }
+        const int off = tc_offset(row, 8 * q, kpad);
+        *reinterpret_cast<uint4 *>(dst + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if (FMT == 2) *reinterpret_cast<uint4 *>(dst + term_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     if (threadIdx.x == 0) scale_out[g.blk0 + b] = scale;
 }

@@ -99,23 +99,38 @@ static bf_status launch_slot(bf_server srv, Slot &slot, bf_precision prec, const
 }
 
 static void dispatcher(bf_server srv) {
+    // Only this thread changes the slots, so their events are queried without
+    // the queue lock; submitters never wait behind a poll.
+    std::vector<int> busy_idx;
+    std::vector<char> done_flag;
+    std::vector<bf_status> done_st;
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
         bool any_busy = false, progressed = false;
         // 1. completions
-        const int64_t now = bf_now_ns();
-        for (Slot &sl : srv->slots) {
-            if (!sl.busy) continue;
-            bool done;
-            bf_status st = BF_OK;
+        busy_idx.clear();
+        for (int i = 0; i < (int)srv->slots.size(); ++i)
+            if (srv->slots[i].busy) busy_idx.push_back(i);
+        lk.unlock();
+        done_flag.assign(busy_idx.size(), 0);
+        done_st.assign(busy_idx.size(), BF_OK);
+        const int64_t t_query = bf_now_ns();
+        for (size_t k = 0; k < busy_idx.size(); ++k) {
+            const Slot &sl = srv->slots[busy_idx[k]];
             if (srv->fake) {
-                done = now >= sl.fake_done_ns;
+                done_flag[k] = t_query >= sl.fake_done_ns;
             } else {
                 const cudaError_t e = cudaEventQuery(sl.ev);
-                done = e != cudaErrorNotReady;
-                if (done && e != cudaSuccess) st = BF_ECUDA;
+                done_flag[k] = e != cudaErrorNotReady;
+                if (done_flag[k] && e != cudaSuccess) done_st[k] = BF_ECUDA;
             }
-            if (!done) {
+        }
+        const int64_t now = bf_now_ns();
+        lk.lock();
+        for (size_t k = 0; k < busy_idx.size(); ++k) {
+            Slot &sl = srv->slots[busy_idx[k]];
+            const bf_status st = done_st[k];
+            if (!done_flag[k]) {
                 any_busy = true;
                 continue;
             }
@@ -199,9 +214,9 @@ static void dispatcher(bf_server srv) {
         if (!any_busy && (srv->queue.empty() || srv->paused)) {
             srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         } else if (!progressed) {
-            // launches in flight: poll completion with short pauses
+            // launches in flight: keep polling, giving the core away between polls
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(2));
+            std::this_thread::yield();
             lk.lock();
         }
     }

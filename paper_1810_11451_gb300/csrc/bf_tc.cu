@@ -42,13 +42,37 @@ constexpr int TC_NACC = 4;       // accumulators in tensor memory
 constexpr int TC_ACC_COLS = 128; // N
 constexpr int TC_RAW_STAGE = 2 * F_LIMIT * S_BYTES_PER_F;  // two complex64 blocks, 34,560 B
 
+// Ring depths per form as three digits: W buffers, operand stages, raw
+// complex64 stages. Chosen by measurement; each may be overridden at compile
+// time (e.g. -DBF_TC_SPLIT_C64_STAGES=123).
+#ifndef BF_TC_SPLIT_C64_STAGES
+#define BF_TC_SPLIT_C64_STAGES 122
+#endif
+#ifndef BF_TC_SPLIT_HELD_STAGES
+#define BF_TC_SPLIT_HELD_STAGES 220
+#endif
+#ifndef BF_TC_SINGLE_C64_STAGES
+#define BF_TC_SINGLE_C64_STAGES 252
+#endif
+#ifndef BF_TC_SINGLE_HELD_STAGES
+#define BF_TC_SINGLE_HELD_STAGES 220
+#endif
+struct Stages {
+    int nw, na, nr;
+};
+constexpr Stages decode_stages(int code) { return {code / 100, (code / 10) % 10, code % 10}; }
+constexpr Stages STAGES[2][2] = {
+    {decode_stages(BF_TC_SINGLE_C64_STAGES), decode_stages(BF_TC_SINGLE_HELD_STAGES)},
+    {decode_stages(BF_TC_SPLIT_C64_STAGES), decode_stages(BF_TC_SPLIT_HELD_STAGES)}};
+
 template <int TERMS, bool HELD>
 struct TcCfg {
     static constexpr int A_TERMS = TERMS == 3 ? 2 : 1;  // hi (and lo) operand images
     static constexpr int W_TERMS = TERMS == 3 ? 2 : 1;
-    static constexpr int NW = (TERMS == 3 && !HELD) ? 1 : 2;
-    static constexpr int NA = HELD ? (TERMS == 3 ? 3 : 4) : (TERMS == 3 ? 2 : 3);
-    static constexpr int NR = HELD ? 0 : (TERMS == 3 ? 2 : 3);
+    static constexpr Stages ST = STAGES[TERMS == 3 ? 1 : 0][HELD ? 1 : 0];
+    static constexpr int NW = ST.nw;
+    static constexpr int NA = ST.na;
+    static constexpr int NR = HELD ? 0 : ST.nr;
     static constexpr int W_BUF = W_TERMS * TC_IMG_MAX;
     static constexpr int A_STAGE = A_TERMS * TC_IMG_MAX;
     static constexpr int OFF_W = 0;

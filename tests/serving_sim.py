@@ -1,0 +1,129 @@
+"""Serving simulation: cells emit one beamforming job per 0.5 ms TTI in real
+time into a `bf_serve` server; the result is per-job latency (scheduled
+arrival to host-observed completion) and throughput.
+
+Workload (the serving recipe of `workloads.serving_schedule`): 8 cells, arrival
+t = 0.5 ms * tti + N(0, 50 us); n_rb ~ U{25..273} resource blocks x 14
+symbols per job; f ~ U{1..36} per cell per 10-TTI precoder epoch; the
+precoders of a cell are re-set every epoch into one of two slot banks.
+Device-resident pools stand in for the radio: per cell a seeded S pool of
+273 x 14 blocks (read with the epoch's f), a shared seeded pool of unit-column
+precoders for every f, and a ring of R buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+
+import numpy as np
+
+import paper_1810_11451_gb300 as bf
+import workloads as wl
+
+N_RB_MAX, N_SYM = 273, 14
+
+
+def _c64(arr, torch):
+    return torch.from_numpy(np.ascontiguousarray(arr.astype(np.complex64)).view(np.float32)).cuda()
+
+
+class ServingSim:
+    def __init__(self, plan, torch, n_cells=8, seed=5, r_ring=4, prec=bf.BF_BF16X3, budget=8 << 30,
+                 n_slots=4, max_batch_jobs=16):
+        self.torch, self.plan, self.n_cells, self.prec = torch, plan, n_cells, prec
+        rng = np.random.default_rng(seed)
+        # shared precoder pool: for every f, 273 unit-column 64 x f precoders
+        self.W = {f: _c64(np.concatenate([wl.precoder_unit_columns(rng, 64, f).ravel() for _ in range(N_RB_MAX)]),
+                          torch) for f in range(1, 37)}
+        # per cell: S pool sized for f = 36 (a prefix is read at smaller f), R ring
+        self.S = [_c64(wl.qam_symbols(rng, 64, (N_RB_MAX * N_SYM * 36 * 60,)), torch) for _ in range(n_cells)]
+        self.R = [[torch.empty(N_RB_MAX * N_SYM * 64 * 60 * 2, device="cuda") for _ in range(r_ring)]
+                  for _ in range(n_cells)]
+        torch.cuda.synchronize()
+        self.srv = bf.bf_serve_create(plan, n_slots=n_slots, max_batch_jobs=max_batch_jobs,
+                                      queue_capacity=1 << 16, hbm_budget_bytes=budget)
+        self._L = bf._serve_sigs(bf.lib())
+        # every cell's full-band group array per (bank, f), built before the
+        # real-time loop so that a submit only fills one job struct
+        self._groups = {}
+        for c in range(n_cells):
+            for bank in range(2):
+                for f in range(1, 37):
+                    self.groups(c, bank, N_RB_MAX, f)
+
+    def slot_base(self, cell, bank):
+        return (cell * 2 + bank) * N_RB_MAX
+
+    def groups(self, cell, bank, n_rb, f):
+        """The job's groups: the first n_rb entries of the cell's full-band
+        group array for (bank, f), built once."""
+        key = (cell, bank, f)
+        g = self._groups.get(key)
+        if g is None:
+            base = self.slot_base(cell, bank)
+            blk_s = N_SYM * f * 480
+            g = bf.make_groups([(base + rb, N_SYM, rb * blk_s, rb * N_SYM * 30720) for rb in range(N_RB_MAX)])[0]
+            self._groups[key] = g
+        return g, n_rb
+
+    def run(self, jobs, warm_tti=20):
+        """Submit `jobs` (workloads.ServingJob, sorted by arrival) in real time.
+        Returns a dict of latency percentiles and throughput."""
+        L, srv = self._L, self.srv
+        # precoders of every cell's first epoch
+        epoch_of_cell = {}
+        t0 = bf.bf_now_ns() + 20_000_000  # start 20 ms from now
+        tickets, meta = [], []
+        ring_pos = [0] * self.n_cells
+        blocks = flops = 0
+        job = bf.bf_job()
+        tk = ctypes.c_uint64()
+        late = 0
+        for j in jobs:
+            e = epoch_of_cell.get(j.cell)
+            if e != j.epoch:
+                bank = j.epoch % 2
+                bf.bf_serve_set_precoders(srv, self.W[j.f], [j.f] * N_RB_MAX, self.slot_base(j.cell, bank))
+                epoch_of_cell[j.cell] = j.epoch
+            arrival = t0 + int(j.arrival_s * 1e9)
+            while bf.bf_now_ns() < arrival:
+                pass
+            if bf.bf_now_ns() - arrival > 50_000:
+                late += 1
+            ga, n = self.groups(j.cell, j.epoch % 2, j.n_rb, j.f)
+            R = self.R[j.cell][ring_pos[j.cell]]
+            ring_pos[j.cell] = (ring_pos[j.cell] + 1) % len(self.R[j.cell])
+            job.cell, job.n_groups, job.groups, job.prec = j.cell, n, ga, self.prec
+            job.S_dev, job.R_dev, job.arrival_ns = self.S[j.cell].data_ptr(), R.data_ptr(), arrival
+            st = L.bf_submit(srv, ctypes.byref(job), ctypes.byref(tk))
+            if st != bf.BF_OK:
+                raise bf.BfError(st, bf.bf_last_error(None))
+            tickets.append(tk.value)
+            meta.append(j)
+            if j.tti >= warm_tti:
+                blocks += j.n_rb * N_SYM
+                flops += j.n_rb * N_SYM * 8 * 64 * 60 * j.f
+        t_last_submit = bf.bf_now_ns()
+        lat = []
+        for t, j in zip(tickets, meta):
+            v = bf.bf_wait(srv, t, 30_000_000)
+            if j.tti >= warm_tti:
+                lat.append(v)
+        t_end = bf.bf_now_ns()
+        stats = bf.bf_serve_get_stats(srv)
+        lat = np.array(lat)
+        span = (t_last_submit - t0) * 1e-9
+        return {
+            "jobs": len(lat), "cells": self.n_cells, "ttis": int(max(j.tti for j in jobs) + 1),
+            "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "max_us": float(lat.max()), "mean_us": float(lat.mean()),
+            "frac_over_500us": float(np.mean(lat > 500.0)),
+            "blocks_per_s": blocks / span, "gflops": flops / span / 1e9,
+            "late_submits": late, "drain_ms": (t_end - t_last_submit) * 1e-6,
+            "launches": stats["launches"], "max_busy_slots": stats["max_busy_slots"],
+            "max_jobs_per_launch": stats["max_jobs_per_launch"], "budget_waits": stats["budget_waits"],
+            "max_inflight_bytes": stats["max_inflight_bytes"],
+        }
+
+    def close(self):
+        bf.bf_serve_destroy(self.srv)

@@ -236,3 +236,55 @@ def test_deterministic(plan):
         a = run(plan, batch, prec, torch)
         b = run(plan, batch, prec, torch, set_w=False)
         assert all(np.array_equal(x.view(np.uint64), y.view(np.uint64)) for x, y in zip(a, b))
+
+
+def test_autotune_keeps_results_and_round_trips(plan, tmp_path):
+    """Tuning changes tile sizes and the CTA split, never a result bit; the
+    table survives a save/load round trip."""
+    batch = wl.config_uneven(seed=12, n_blocks=900)
+    before = {p: run(plan, batch, p, torch) for p in (bf.BF_FP32, bf.BF_BF16X3)}
+    for p in (bf.BF_FP32, bf.BF_BF16X3):
+        bf.bf_autotune(plan, p)
+        q = [bf.bf_tune_query(plan, p, f) for f in (0, 8, 16, 24, 36)]
+        assert all(e["tuned"] and e["ns_per_block"] > 0 and e["tile_blocks"] in (1, 2) for e in q), q
+        after = run(plan, batch, p, torch)
+        for x, y in zip(before[p], after):
+            assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+    path = str(tmp_path / "tune.json")
+    bf.bf_tune_save(plan, path)
+    saved = [bf.bf_tune_query(plan, bf.BF_BF16X3, f) for f in (0, 8, 16, 24, 36)]
+    other = bf.bf_plan_create(64, 36, 60)
+    try:
+        assert not bf.bf_tune_query(other, bf.BF_BF16X3, 36)["tuned"]
+        bf.bf_tune_load(other, path)
+        got = [bf.bf_tune_query(other, bf.BF_BF16X3, f) for f in (0, 8, 16, 24, 36)]
+        assert all(abs(a["ns_per_block"] - b["ns_per_block"]) < 1e-5 and a["tile_blocks"] == b["tile_blocks"]
+                   for a, b in zip(saved, got))
+        with open(path, "w") as fh:
+            fh.write("{}")
+        with pytest.raises(bf.BfError):
+            bf.bf_tune_load(other, path)
+    finally:
+        bf.bf_plan_destroy(other)
+
+
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4]], ids=["fp32", "bf16x3", "bf16_held"])
+def test_uneven_full_size(plan, name, prec, held):
+    """The uneven workload at full size (16,384 blocks) in one persistent launch,
+    checked in full against the oracle."""
+    batch = wl.config_uneven()
+    R = run(plan, batch, prec, torch, held=held, mode="batch")
+    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    e = _assert_close(R, ref, _tol(prec), name)
+    print(f"uneven full size {name}: {e:.3e}")
+
+
+@pytest.mark.parametrize("name,prec,held", [FORMS[1], FORMS[2], FORMS[4], FORMS[6]],
+                         ids=["bf16x3", "bf16x3_held", "bf16_held", "fp16_held"])
+def test_reduced_full_size(plan, name, prec, held):
+    """The reduced-precision workload at full size (30,576 blocks, 2,184 precoders)."""
+    batch = wl.config_reduced()
+    R = run(plan, batch, prec, torch, held=held, mode="batch")
+    ref = _ref(batch) if prec == bf.BF_BF16X3 else oracle.apply_batch(batch)
+    e = _assert_close(R, ref, _tol(prec), name)
+    print(f"reduced full size {name}: {e:.3e}")
