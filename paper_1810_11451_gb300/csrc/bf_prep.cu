@@ -126,10 +126,24 @@ __global__ void __launch_bounds__(256) bf_quantize_kernel(const uint8_t *__restr
     if (b >= g.nb) return;
     const int f = g.f, kpad = kpad_of(f);
     const float2 *s = reinterpret_cast<const float2 *>(S + g.s_off + (int64_t)b * f * S_BYTES_PER_F);
+    // One task = one row (resource element j) and one 8-column chunk q (flows
+    // 4q..4q+3): consecutive threads take consecutive rows, so the reads of a
+    // warp cover 256 contiguous bytes of one flow row of S and its writes 16
+    // contiguous bytes per row, 128 per 8 rows. The block is read once into
+    // registers (all loads in flight together), reduced, then encoded.
+    constexpr int NT = 256, MAXT = (64 * (KPAD_MAX / 8) + NT - 1) / NT;
+    const int n_tasks = 64 * (kpad / 8);
+    float2 v[MAXT][4];
     float m = 0.f;
-    for (int e = threadIdx.x; e < f * B_RE; e += blockDim.x) {
-        const float2 v = s[e];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+#pragma unroll
+    for (int i = 0; i < MAXT; ++i) {
+        const int e = threadIdx.x + i * NT, q = e >> 6, row = e & 63;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * q + u;
+            v[i][u] = (e < n_tasks && row < B_RE && k < f) ? s[k * B_RE + row] : make_float2(0.f, 0.f);
+            m = fmaxf(m, fmaxf(fabsf(v[i][u].x), fabsf(v[i][u].y)));
+        }
     }
     m = block_max(m, red);
     const int ex = m > 0.f ? ceil_log2_exact(m) : 0;
@@ -138,19 +152,14 @@ __global__ void __launch_bounds__(256) bf_quantize_kernel(const uint8_t *__restr
     constexpr int TERMS = FMT == 2 ? 2 : 1;
     uint8_t *dst = Sq + g.q_off + (int64_t)b * held_block_bytes(f, TERMS);
     const int term_bytes = 64 * kpad * 2;
-    // One task = one row (resource element j) and one 8-column chunk q (flows
-    // 4q..4q+3): consecutive threads take consecutive rows, so the reads of a
-    // warp cover 256 contiguous bytes of one flow row of S and its writes 16
-    // contiguous bytes per row, 128 per 8 rows.
-    for (int e = threadIdx.x; e < 64 * (kpad / 8); e += blockDim.x) {
-        const int q = e >> 6, row = e & 63;
+#pragma unroll
+    for (int i = 0; i < MAXT; ++i) {
+        const int e = threadIdx.x + i * NT, q = e >> 6, row = e & 63;
+        if (e >= n_tasks) break;
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int k = 4 * q + u;
-            float2 v = make_float2(0.f, 0.f);
-            if (row < B_RE && k < f) v = s[k * B_RE + row];
-            const float xr = v.x * inv, xi = v.y * inv;
+            const float xr = v[i][u].x * inv, xi = v[i][u].y * inv;
             if (FMT == 1) {
                 const __half2 h = __floats2half2_rn(xr, xi);
                 hi[u] = *reinterpret_cast<const uint32_t *>(&h);

@@ -37,7 +37,20 @@
 
 namespace bfi {
 
-constexpr int TC_THREADS = 384;
+// Converter and epilogue warps (the epilogue count a multiple of 4: warp w
+// reads tensor-memory lanes 32*(w%4) .. 32*(w%4)+31).
+#ifndef BF_TC_CONV_WARPS
+#define BF_TC_CONV_WARPS 4
+#endif
+#ifndef BF_TC_EPI_WARPS
+#define BF_TC_EPI_WARPS 4
+#endif
+constexpr int TC_CONV_WARPS = BF_TC_CONV_WARPS;
+constexpr int TC_EPI_WARPS = BF_TC_EPI_WARPS;
+static_assert(TC_CONV_WARPS % 4 == 0 && TC_EPI_WARPS % 4 == 0 && TC_EPI_WARPS <= 16, "warp counts");
+constexpr int TC_CONV0 = 4;                          // first converter warp
+constexpr int TC_EPI0 = TC_CONV0 + TC_CONV_WARPS;    // first epilogue warp (a multiple of 4)
+constexpr int TC_THREADS = 32 * (TC_EPI0 + TC_EPI_WARPS);
 constexpr int TC_NACC = 4;       // accumulators in tensor memory
 constexpr int TC_ACC_COLS = 128; // N
 constexpr int TC_RAW_STAGE = 2 * F_LIMIT * S_BYTES_PER_F;  // two complex64 blocks, 34,560 B
@@ -49,13 +62,13 @@ constexpr int TC_RAW_STAGE = 2 * F_LIMIT * S_BYTES_PER_F;  // two complex64 bloc
 #define BF_TC_SPLIT_C64_STAGES 122
 #endif
 #ifndef BF_TC_SPLIT_HELD_STAGES
-#define BF_TC_SPLIT_HELD_STAGES 220
+#define BF_TC_SPLIT_HELD_STAGES 120
 #endif
 #ifndef BF_TC_SINGLE_C64_STAGES
 #define BF_TC_SINGLE_C64_STAGES 252
 #endif
 #ifndef BF_TC_SINGLE_HELD_STAGES
-#define BF_TC_SINGLE_HELD_STAGES 220
+#define BF_TC_SINGLE_HELD_STAGES 120
 #endif
 struct Stages {
     int nw, na, nr;
@@ -123,10 +136,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::NR; ++s) {
             bfd::mbar_init(raw_full(s), 1);
-            bfd::mbar_init(raw_empty(s), 4);
+            bfd::mbar_init(raw_empty(s), TC_CONV_WARPS);
         }
         for (int s = 0; s < C::NA; ++s) {
-            bfd::mbar_init(a_full(s), HELD ? 1 : 4);
+            bfd::mbar_init(a_full(s), HELD ? 1 : TC_CONV_WARPS);
             bfd::mbar_init(a_empty(s), 1);
         }
         for (int s = 0; s < C::NW; ++s) {
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
         }
         for (int s = 0; s < TC_NACC; ++s) {
             bfd::mbar_init(acc_full(s), 1);
-            bfd::mbar_init(acc_empty(s), 4);
+            bfd::mbar_init(acc_empty(s), TC_EPI_WARPS);
         }
         bfd::mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -244,11 +257,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
             bfd::umma_commit(drain_bar);
             bfd::mbar_wait_drain(drain_bar, 0, 1000000000ull);
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp >= TC_CONV0 && warp < TC_EPI0) {
         // ---------------- converters (complex64 S -> operand images) ----------------
         if constexpr (!HELD) {
-            const int tid = threadIdx.x - 128;
-            const int blk = tid >> 6, j = tid & 63;
+            // thread -> (block of the tile, resource element j, first K chunk);
+            // with more than 4 converter warps the K chunks are interleaved
+            const int tid = threadIdx.x - 32 * TC_CONV0;
+            const int blk = (tid >> 6) & 1, j = tid & 63, q0 = tid >> 7;
+            constexpr int QSTEP = TC_CONV_WARPS / 4;
             int n = 0;
             for (int t = t0; t < t1; ++t) {
                 const Tile tl = p.tiles[t];
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                     const int kp = kpad_of(f);
                     const int row = 64 * blk + j;
                     uint8_t *dst = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
-                    for (int q = 0; q < kp / 8; ++q) {
+                    for (int q = q0; q < kp / 8; q += QSTEP) {
                         float v[8];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -299,11 +315,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 ++n;
             }
         }
-    } else if (warp >= 8) {
+    } else if (warp >= TC_EPI0) {
         // ---------------- epilogue ----------------
-        const int q = warp - 8;               // tensor-memory lane quadrant
-        const int blk = q >> 1;               // block of the tile
-        const int j = (q & 1) * 32 + lane;    // resource element
+        const int q = warp & 3;                       // tensor-memory lane quadrant
+        const int blk = q >> 1;                       // block of the tile
+        const int j = (q & 1) * 32 + lane;            // resource element
+        constexpr int NCH = 4 / (TC_EPI_WARPS / 4);   // 32-column chunks per warp
+        const int c0 = ((warp - TC_EPI0) >> 2) * NCH; // first chunk of this warp
         int n = 0;
         for (int t = t0; t < t1; ++t) {
             const Tile tl = p.tiles[t];
@@ -311,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
             float2 *rrow = reinterpret_cast<float2 *>(p.R + tl.r_off + (int64_t)blk * R_BLOCK_BYTES) + j;
             if (tl.f == 0) {
                 if (live)
-                    for (int i = 0; i < N_ANT; ++i) rrow[i * B_RE] = make_float2(0.f, 0.f);
+                    for (int i = 16 * c0; i < 16 * (c0 + NCH); ++i) rrow[i * B_RE] = make_float2(0.f, 0.f);
                 continue;
             }
             const int d = n % TC_NACC;
@@ -321,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
             if (HELD) scale *= p.s_scale[tl.sblk + (blk < tl.nblk ? blk : 0)];
             const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + d * TC_ACC_COLS;
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
+            for (int c = c0; c < c0 + NCH; ++c) {
                 uint32_t v[32];
                 bfd::tmem_ld32(ta + 32 * c, v);
                 bfd::tmem_ld_wait();
