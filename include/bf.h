@@ -172,15 +172,20 @@ bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *
                               int32_t n_groups, bf_precision prec, void *R_host,
                               void *stream);
 
-/* A prepared batch: the work list is built and uploaded once and the launch
- * is captured in a CUDA graph, so bf_batch_launch is a single graph replay.
- * Arguments as bf_apply_batch; the buffers must stay valid for the batch's
- * lifetime. */
+/* A prepared batch: the work list is built and uploaded once, and the one
+ * persistent launch is also captured in a CUDA graph. Arguments as
+ * bf_apply_batch; the buffers must stay valid for the batch's lifetime.
+ *  bf_batch_launch       : launches the kernel directly on `stream` (the
+ *                          cheapest form; it may itself be captured into a
+ *                          caller's graph).
+ *  bf_batch_launch_graph : replays the batch's own captured graph on `stream`.
+ * Both compute the same bits. */
 typedef struct bf_batch_s *bf_batch;
 bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev,
                           const bf_group *groups, int32_t n_groups, bf_precision prec,
                           void *R_dev, bf_batch *out);
 bf_status bf_batch_launch(bf_batch batch, void *stream);
+bf_status bf_batch_launch_graph(bf_batch batch, void *stream);
 bf_status bf_batch_destroy(bf_batch batch);
 
 /* ------------------------------------------------------------------ scheduler */

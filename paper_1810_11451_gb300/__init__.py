@@ -116,16 +116,30 @@ def _stream(s) -> Optional[int]:
     return int(s.cuda_stream) or None
 
 
-def make_groups(groups: Iterable) -> Tuple[ctypes.Array, int]:
-    """ctypes array of bf_group from (prec_id, n_blocks, s_off, r_off) tuples."""
-    gl = list(groups)
-    arr = (bf_group * max(1, len(gl)))()
-    for i, g in enumerate(gl):
-        if isinstance(g, bf_group):
-            arr[i] = g
-        else:
-            arr[i] = bf_group(int(g[0]), int(g[1]), int(g[2]), int(g[3]))
-    return arr, len(gl)
+_GROUP_DTYPE = None
+
+
+def make_groups(groups) -> Tuple[ctypes.Array, int]:
+    """ctypes array of bf_group from (prec_id, n_blocks, s_off, r_off) rows: a
+    list of tuples, an (n, 4) integer array, or an existing ctypes bf_group
+    array (passed through). Built through numpy, so large lists are cheap."""
+    global _GROUP_DTYPE
+    if isinstance(groups, ctypes.Array) and groups._type_ is bf_group:
+        return groups, len(groups)
+    import numpy as np
+    if _GROUP_DTYPE is None:
+        _GROUP_DTYPE = np.dtype([("prec_id", "<i4"), ("n_blocks", "<i4"), ("s_off", "<i8"), ("r_off", "<i8")])
+        assert _GROUP_DTYPE.itemsize == ctypes.sizeof(bf_group)
+    rows = np.asarray(groups if not isinstance(groups, (list, tuple)) or len(groups) else np.zeros((0, 4)),
+                      dtype=np.int64).reshape(-1, 4)
+    st = np.zeros(max(1, len(rows)), dtype=_GROUP_DTYPE)
+    if len(rows):
+        st["prec_id"][:len(rows)] = rows[:, 0]
+        st["n_blocks"][:len(rows)] = rows[:, 1]
+        st["s_off"][:len(rows)] = rows[:, 2]
+        st["r_off"][:len(rows)] = rows[:, 3]
+    arr = (bf_group * len(st)).from_buffer(st)
+    return arr, len(rows)
 
 
 def _check(status: int, plan=None):
@@ -194,9 +208,20 @@ def bf_batch_create(plan, S_dev, scale_dev, groups, prec: int, R_dev) -> int:
 
 
 def bf_batch_launch(batch, stream=None) -> None:
+    """Launch a prepared batch directly (one persistent kernel)."""
     st = lib().bf_batch_launch(batch, _stream(stream))
     if st != BF_OK:
         raise BfError(st, "bf_batch_launch failed")
+
+
+def bf_batch_launch_graph(batch, stream=None) -> None:
+    """Replay the prepared batch's captured CUDA graph."""
+    L = lib()
+    L.bf_batch_launch_graph.restype = c_int
+    L.bf_batch_launch_graph.argtypes = [c_void_p, c_void_p]
+    st = L.bf_batch_launch_graph(batch, _stream(stream))
+    if st != BF_OK:
+        raise BfError(st, "bf_batch_launch_graph failed")
 
 
 def bf_batch_destroy(batch) -> None:

@@ -540,6 +540,10 @@ struct bf_batch_s {
     uint8_t *d = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    KParams p{};
+    int n_cta = 0;
+    bf_precision prec = BF_FP32;
+    bool held = false;
 };
 
 extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
@@ -568,10 +572,13 @@ extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const floa
             return bf_fail(plan, BF_ECUDA, "work-list upload: %s", cudaGetErrorString(e));
         }
     }
+    bt->p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec);
+    bt->n_cta = wl.tiles.empty() ? 0 : (int)wl.cta_begin.size() - 1;
+    bt->prec = prec;
+    bt->held = scale_dev != nullptr;
     cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess && !wl.tiles.empty()) {
-        const KParams p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec);
-        cudaError_t le = launch_kernel(prec, scale_dev != nullptr, p, (int)wl.cta_begin.size() - 1, plan->cap_stream);
+    if (e == cudaSuccess && bt->n_cta > 0) {
+        cudaError_t le = launch_kernel(prec, bt->held, bt->p, bt->n_cta, plan->cap_stream);
         if (le != cudaSuccess) e = le;
     }
     cudaError_t ee = cudaStreamEndCapture(plan->cap_stream, &bt->graph);
@@ -587,6 +594,14 @@ extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const floa
 }
 
 extern "C" bf_status bf_batch_launch(bf_batch batch, void *stream) {
+    if (!batch) return bf_fail(nullptr, BF_EINVAL, "batch is NULL");
+    bf_plan plan = batch->plan;
+    if (batch->n_cta > 0) BF_CK(plan, launch_kernel(batch->prec, batch->held, batch->p, batch->n_cta, (cudaStream_t)stream));
+    plan->launches++;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_batch_launch_graph(bf_batch batch, void *stream) {
     if (!batch) return bf_fail(nullptr, BF_EINVAL, "batch is NULL");
     bf_plan plan = batch->plan;
     BF_CK(plan, cudaGraphLaunch(batch->exec, (cudaStream_t)stream));

@@ -94,9 +94,9 @@ def run(plan, batch, prec: int, torch, held: bool = False, mode: str = "apply", 
         groups = [(g[0], g[1], lay.held_off[i], g[3]) for i, g in enumerate(lay.groups)]
     if mode == "apply":
         bf.bf_apply_batch(plan, S_use, scale, groups, prec, R_t)
-    elif mode == "batch":
+    elif mode in ("batch", "graph"):
         h = bf.bf_batch_create(plan, S_use, scale, groups, prec, R_t)
-        bf.bf_batch_launch(h)
+        (bf.bf_batch_launch if mode == "batch" else bf.bf_batch_launch_graph)(h)
         torch.cuda.synchronize()
         bf.bf_batch_destroy(h)
     else:

@@ -168,13 +168,10 @@ def test_graph_and_host_paths_bitwise(plan):
     batch = wl.config_uneven(seed=9, n_blocks=400)
     for prec in (bf.BF_FP32, bf.BF_BF16X3):
         a = run(plan, batch, prec, torch, mode="apply")
-        b = run(plan, batch, prec, torch, mode="batch", set_w=False)
-        c = run(plan, batch, prec, torch, mode="host", set_w=False)
-        d = run(plan, batch, prec, torch, mode="apply", set_w=False)
-        for x, y, z, w in zip(a, b, c, d):
-            assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
-            assert np.array_equal(x.view(np.uint64), z.view(np.uint64))
-            assert np.array_equal(x.view(np.uint64), w.view(np.uint64))
+        others = [run(plan, batch, prec, torch, mode=m, set_w=False) for m in ("batch", "graph", "host", "apply")]
+        for o in others:
+            for x, y in zip(a, o):
+                assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
 
 
 def test_fullband_full_size(plan):

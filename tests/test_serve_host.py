@@ -62,10 +62,10 @@ def test_budget_limits_inflight_bytes(bf):
 
 
 def test_continuous_batching_merges_and_overlaps(bf):
-    srv = bf.bf_serve_create(None, n_slots=2, max_batch_jobs=8, hbm_budget_bytes=1 << 34, fake_device_us=2000)
+    srv = bf.bf_serve_create(None, n_slots=2, max_batch_jobs=8, hbm_budget_bytes=1 << 34, fake_device_us=50000)
     try:
         first = bf.bf_submit(srv, job_groups(1), bf.BF_BF16X3, FAKE_S, FAKE_R)
-        time.sleep(0.0005)
+        time.sleep(0.005)
         # these arrive while the first launch runs: they start at once on the
         # second slot, merged into one launch
         rest = [bf.bf_submit(srv, job_groups(1), bf.BF_BF16X3, FAKE_S, FAKE_R) for _ in range(6)]
