@@ -78,6 +78,16 @@ static __device__ __noinline__ void mbar_wait_drain(uint32_t bar, uint32_t parit
     }
 }
 
+// ------------------------------------------------------------------ dependent launch
+// Let the next kernel on the stream start its prologue on SMs this grid frees
+// (every CTA calls this once it holds its resources).
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Wait until the grids this one depends on have completed and their memory
+// is visible; nothing in global memory is touched before this.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------ bulk copies
 // Global -> shared bulk copy completing on an mbarrier (both addresses 16-byte
 // aligned, size a multiple of 16).

@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
     auto w_empty = [&](int w) { return bar0 + 8u * (2 * SIMT_NS + SIMT_NW + w); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SIMT_NS; ++s) {
@@ -56,6 +55,11 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
         bfd::mbar_init_fence();
     }
     __syncthreads();
+    // No global memory touched yet: let the next launch start its prologue,
+    // then wait for the previous kernel on the stream to finish.
+    bfd::grid_dep_launch();
+    bfd::grid_dep_wait();
+    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == SIMT_CWARPS) {
         // ---------------- producer ----------------
@@ -187,8 +191,17 @@ cudaError_t configure_simt() {
 }
 
 cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream) {
-    bf_simt_kernel<<<n_cta, SIMT_THREADS, SIMT_SMEM, stream>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_cta);
+    cfg.blockDim = dim3(SIMT_THREADS);
+    cfg.dynamicSmemBytes = SIMT_SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see grid_dep_wait
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bf_simt_kernel, p);
 }
 
 int simt_smem_bytes() { return SIMT_SMEM; }

@@ -130,7 +130,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     const uint32_t drain_bar = bar0 + 8u * (C::NBARS - 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
     constexpr uint32_t IDESC = bfd::idesc_f16(BF16, 128, TC_ACC_COLS);
 
     if (threadIdx.x == 0) {
@@ -162,6 +161,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     __syncthreads();
     bfd::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // The prologue above touched no global memory: let the next launch on the
+    // stream begin its own, then wait for the previous one to finish.
+    bfd::grid_dep_launch();
+    bfd::grid_dep_wait();
+    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == 0) {
         // ---------------- S producer ----------------
@@ -372,8 +376,19 @@ static cudaError_t configure_tc_t() {
 
 template <int TERMS, bool HELD, bool BF16>
 static cudaError_t launch_tc_t(const KParams &p, int n_cta, cudaStream_t stream) {
-    bf_tc_kernel<TERMS, HELD, BF16><<<n_cta, TC_THREADS, TcCfg<TERMS, HELD>::SMEM, stream>>>(p);
-    return cudaGetLastError();
+    // Programmatic stream serialization: this launch may begin its prologue
+    // while the previous kernel on the stream finishes (see grid_dep_wait).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_cta);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TcCfg<TERMS, HELD>::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bf_tc_kernel<TERMS, HELD, BF16>, p);
 }
 
 // Raise every instance's dynamic shared-memory limit (once, before launches).
