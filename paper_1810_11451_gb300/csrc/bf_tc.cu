@@ -53,19 +53,20 @@ constexpr int TC_EPI0 = TC_CONV0 + TC_CONV_WARPS;    // first epilogue warp (a m
 constexpr int TC_THREADS = 32 * (TC_EPI0 + TC_EPI_WARPS);
 constexpr int TC_NACC = 4;       // accumulators in tensor memory
 constexpr int TC_ACC_COLS = 128; // N
-constexpr int TC_RAW_STAGE = 2 * F_LIMIT * S_BYTES_PER_F;  // two complex64 blocks, 34,560 B
+constexpr int TC_RAW_SLOT = F_LIMIT * S_BYTES_PER_F;  // one complex64 block, 17,280 B
+constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shared memory per CTA
 
-// Ring depths per form as three digits: W buffers, operand stages, raw
-// complex64 stages. Chosen by measurement; each may be overridden at compile
-// time (e.g. -DBF_TC_SPLIT_C64_STAGES=123).
+// Ring depths per form as three digits: W buffers, operand stages (tiles),
+// raw complex64 slots (blocks). Chosen by measurement; each may be
+// overridden at compile time (e.g. -DBF_TC_SPLIT_C64_STAGES=223).
 #ifndef BF_TC_SPLIT_C64_STAGES
-#define BF_TC_SPLIT_C64_STAGES 122
+#define BF_TC_SPLIT_C64_STAGES 124
 #endif
 #ifndef BF_TC_SPLIT_HELD_STAGES
 #define BF_TC_SPLIT_HELD_STAGES 120
 #endif
 #ifndef BF_TC_SINGLE_C64_STAGES
-#define BF_TC_SINGLE_C64_STAGES 252
+#define BF_TC_SINGLE_C64_STAGES 253
 #endif
 #ifndef BF_TC_SINGLE_HELD_STAGES
 #define BF_TC_SINGLE_HELD_STAGES 120
@@ -91,10 +92,12 @@ struct TcCfg {
     static constexpr int OFF_W = 0;
     static constexpr int OFF_A = OFF_W + NW * W_BUF;
     static constexpr int OFF_RAW = OFF_A + NA * A_STAGE;
-    static constexpr int OFF_BAR = OFF_RAW + NR * TC_RAW_STAGE;
+    static constexpr int OFF_BAR = OFF_RAW + NR * TC_RAW_SLOT;
     // raw full/empty, a full/empty, w full/empty, acc full/empty, drain
     static constexpr int NBARS = 2 * NR + 2 * NA + 2 * NW + 2 * TC_NACC + 1;
     static constexpr int SMEM = OFF_BAR + NBARS * 8 + 16;
+    static_assert(SMEM <= SMEM_LIMIT, "ring depths exceed the shared memory of one CTA");
+    static_assert(HELD || NR >= 2, "a two-block tile needs at least two raw slots");
 };
 
 __device__ __forceinline__ uint32_t pack2_bf16(float a, float b) {
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::NR; ++s) {
             bfd::mbar_init(raw_full(s), 1);
-            bfd::mbar_init(raw_empty(s), TC_CONV_WARPS);
+            bfd::mbar_init(raw_empty(s), TC_CONV_WARPS);  // every converter warp reads every slot
         }
         for (int s = 0; s < C::NA; ++s) {
             bfd::mbar_init(a_full(s), HELD ? 1 : TC_CONV_WARPS);
@@ -170,17 +173,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     if (warp == 0) {
         // ---------------- S producer ----------------
         if (lane == 0) {
-            int n = 0;
-            for (int t = t0; t < t1; ++t) {
+            int n = 0, nb = 0;  // tiles and (complex64 input) blocks issued
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
                 const Tile tl = p.tiles[t];
                 if (tl.f == 0) continue;
                 if constexpr (!HELD) {
-                    const int st = n % C::NR;
-                    if (!bfd::mbar_wait(raw_empty(st), ((n / C::NR) + 1) & 1, abort_flag, p.status)) break;
-                    const uint32_t bytes = (uint32_t)(tl.nblk * tl.f * S_BYTES_PER_F);
-                    bfd::mbar_arrive_expect_tx(raw_full(st), bytes);
-                    bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_RAW + st * TC_RAW_STAGE), p.S + tl.s_off,
-                                  bytes, raw_full(st));
+                    // one raw slot per block: blocks of a tile land in consecutive slots
+                    const uint32_t bytes = (uint32_t)(tl.f * S_BYTES_PER_F);
+                    for (int b = 0; b < tl.nblk; ++b, ++nb) {
+                        const int st = nb % C::NR;
+                        if (!bfd::mbar_wait(raw_empty(st), ((nb / C::NR) + 1) & 1, abort_flag, p.status)) {
+                            ok = false;
+                            break;
+                        }
+                        bfd::mbar_arrive_expect_tx(raw_full(st), bytes);
+                        bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_RAW + st * TC_RAW_SLOT),
+                                      p.S + tl.s_off + (int64_t)b * bytes, bytes, raw_full(st));
+                    }
+                    if (!ok) break;
                 } else {
                     const int st = n % C::NA;
                     if (!bfd::mbar_wait(a_empty(st), ((n / C::NA) + 1) & 1, abort_flag, p.status)) break;
@@ -195,8 +206,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 }
                 ++n;
             }
+            // drain: the last copies issued into each ring slot
             constexpr int NS = HELD ? C::NA : C::NR;
-            for (int m = n > NS ? n - NS : 0; m < n; ++m)
+            const int issued = HELD ? n : nb;
+            for (int m = issued > NS ? issued - NS : 0; m < issued; ++m)
                 bfd::mbar_wait_drain(bar0 + 8u * ((HELD ? 2 * C::NR : 0) + m % NS), (m / NS) & 1,
                                      1000000000ull);
         }
@@ -264,58 +277,68 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     } else if (warp >= TC_CONV0 && warp < TC_EPI0) {
         // ---------------- converters (complex64 S -> operand images) ----------------
         if constexpr (!HELD) {
-            // thread -> (block of the tile, resource element j, first K chunk);
-            // with more than 4 converter warps the K chunks are interleaved
+            // thread -> (resource element j, first K chunk q0); every warp
+            // converts part of every block, so all converter warps wait on and
+            // release every raw slot in order. (Warps that skipped slots could
+            // run a ring lap ahead, and a parity wait one phase early passes.)
             const int tid = threadIdx.x - 32 * TC_CONV0;
-            const int blk = (tid >> 6) & 1, j = tid & 63, q0 = tid >> 7;
-            constexpr int QSTEP = TC_CONV_WARPS / 4;
-            int n = 0;
-            for (int t = t0; t < t1; ++t) {
+            const int j = tid & 63, q0 = tid >> 6;
+            constexpr int QSTEP = TC_CONV_WARPS / 2;
+            int n = 0, nb = 0;  // tiles and blocks consumed
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
                 const Tile tl = p.tiles[t];
                 const int f = tl.f;
                 if (f == 0) continue;
-                const int r = n % C::NR, a = n % C::NA;
-                if (!bfd::mbar_wait(raw_full(r), (n / C::NR) & 1, abort_flag, p.status)) break;
+                const int a = n % C::NA;
                 if (!bfd::mbar_wait(a_empty(a), ((n / C::NA) + 1) & 1, abort_flag, p.status)) break;
-                if (blk < tl.nblk && j < B_RE) {
-                    const uint8_t *raw = smem + C::OFF_RAW + r * TC_RAW_STAGE + blk * f * S_BYTES_PER_F;
-                    const int kp = kpad_of(f);
-                    const int row = 64 * blk + j;
-                    uint8_t *dst = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
-                    for (int q = q0; q < kp / 8; q += QSTEP) {
-                        float v[8];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = 4 * q + u;
-                            float2 x = make_float2(0.f, 0.f);
-                            if (k < f) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F + j * 8);
-                            v[2 * u] = x.x;
-                            v[2 * u + 1] = x.y;
-                        }
-                        uint4 hi, lo;
-                        uint32_t *h = &hi.x, *l = &lo.x;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (BF16) {
-                                h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
-                                if (TERMS == 3) {
-                                    const float2 back = unpack2_bf16(h[u]);
-                                    l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
-                                }
-                            } else {
-                                h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
-                            }
-                        }
-                        *reinterpret_cast<uint4 *>(dst + q * 128) = hi;
-                        if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + TC_IMG_MAX + q * 128) = lo;
+                for (int blk = 0; blk < tl.nblk; ++blk, ++nb) {
+                    const int r = nb % C::NR;
+                    if (!bfd::mbar_wait(raw_full(r), (nb / C::NR) & 1, abort_flag, p.status)) {
+                        ok = false;
+                        break;
                     }
+                    if (j < B_RE) {
+                        const uint8_t *raw = smem + C::OFF_RAW + r * TC_RAW_SLOT;
+                        const int kp = kpad_of(f);
+                        const int row = 64 * blk + j;
+                        uint8_t *dst =
+                            smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
+                        for (int q = q0; q < kp / 8; q += QSTEP) {
+                            float v[8];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int k = 4 * q + u;
+                                float2 x = make_float2(0.f, 0.f);
+                                if (k < f) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F + j * 8);
+                                v[2 * u] = x.x;
+                                v[2 * u + 1] = x.y;
+                            }
+                            uint4 hi, lo;
+                            uint32_t *h = &hi.x, *l = &lo.x;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (BF16) {
+                                    h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
+                                    if (TERMS == 3) {
+                                        const float2 back = unpack2_bf16(h[u]);
+                                        l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
+                                    }
+                                } else {
+                                    h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
+                                }
+                            }
+                            *reinterpret_cast<uint4 *>(dst + q * 128) = hi;
+                            if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + TC_IMG_MAX + q * 128) = lo;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) bfd::mbar_arrive(raw_empty(r));  // this warp is done with the slot
                 }
+                if (!ok) break;
                 bfd::fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) {
-                    bfd::mbar_arrive(raw_empty(r));
-                    bfd::mbar_arrive(a_full(a));
-                }
+                if (lane == 0) bfd::mbar_arrive(a_full(a));
                 ++n;
             }
         }

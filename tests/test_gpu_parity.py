@@ -276,6 +276,21 @@ def test_uneven_full_size(plan, name, prec, held):
     print(f"uneven full size {name}: {e:.3e}")
 
 
+@pytest.mark.parametrize("name,prec", [("bf16x3", bf.BF_BF16X3), ("bf16", bf.BF_BF16)])
+def test_uneven_full_size_repeatable(plan, name, prec):
+    """Pipeline races show up as a few wrong blocks that change from run to run:
+    the full-size uneven batch (1- and 2-block tiles, f from 0 to 36, many
+    precoder switches per CTA) must give the same bits five times over."""
+    batch = wl.config_uneven()
+    first = run(plan, batch, prec, torch, mode="batch")
+    ref = _ref(batch) if prec == bf.BF_BF16X3 else oracle.apply_batch(batch)
+    _assert_close(first, ref, _tol(prec), name)
+    for rep in range(4):
+        again = run(plan, batch, prec, torch, mode="batch" if rep % 2 else "apply", set_w=False)
+        for g, (x, y) in enumerate(zip(first, again)):
+            assert np.array_equal(x.view(np.uint64), y.view(np.uint64)), f"{name}: group {g} differs on repeat {rep}"
+
+
 @pytest.mark.parametrize("name,prec,held", [FORMS[1], FORMS[2], FORMS[4], FORMS[6]],
                          ids=["bf16x3", "bf16x3_held", "bf16_held", "fp16_held"])
 def test_reduced_full_size(plan, name, prec, held):
