@@ -124,7 +124,7 @@ extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) 
         // CTAs per SM of the CUDA-core kernel, at f = 36
         double best = 1e30;
         int best_c = T.simt_ctas_per_sm;
-        for (int c = 1; c <= 2; ++c) {
+        for (int c = 1; c <= plan->simt_resident; ++c) {
             T.simt_ctas_per_sm = c;
             double t2 = 0;
             if ((result = time_batch(plan, sc, prec, fs[(TUNE_BUCKETS - 1) * SLOTS_PER_F],
@@ -189,7 +189,7 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
     TuneTable T;
     size_t pos = txt.find("\"simt_ctas_per_sm\":");
     if (pos == std::string::npos || sscanf(txt.c_str() + pos + 19, "%d", &T.simt_ctas_per_sm) != 1 ||
-        T.simt_ctas_per_sm < 1 || T.simt_ctas_per_sm > 2)
+        T.simt_ctas_per_sm < 1 || T.simt_ctas_per_sm > 16)
         return bad("simt_ctas_per_sm");
     for (int p = 0; p < 4; ++p) {
         char key[32];

@@ -129,6 +129,8 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
     p->n_ant = n_ant;
     p->f_max = f_max;
     p->b = b;
+    p->simt_resident = simt_resident_ctas();
+    p->tune.simt_ctas_per_sm = p->simt_resident;
     if (cudaMalloc((void **)&p->d_status, 64) != cudaSuccess || cudaMemset(p->d_status, 0, 64) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -472,7 +474,7 @@ static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_byte
 }
 
 int max_cta_for(bf_plan plan, bf_precision prec) {
-    const int per_sm = prec == BF_FP32 ? plan->tune.simt_ctas_per_sm : 1;
+    const int per_sm = prec == BF_FP32 ? std::max(1, std::min(plan->tune.simt_ctas_per_sm, plan->simt_resident)) : 1;
     return plan->sm_count * per_sm;
 }
 

@@ -25,7 +25,7 @@ struct TuneTable {
     double ns_per_block[4][TUNE_BUCKETS];
     int tile_blocks[4][TUNE_BUCKETS];
     bool tuned[4] = {false, false, false, false};
-    int simt_ctas_per_sm = 2;
+    int simt_ctas_per_sm = 2;  // set to the resident maximum when a plan is created
     TuneTable() {
         for (int p = 0; p < 4; ++p)
             for (int b = 0; b < TUNE_BUCKETS; ++b) {
@@ -62,6 +62,7 @@ struct WorkBuf {
 
 struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
+    int simt_resident = 2;  // CTAs of the CUDA-core kernel that fit on one SM
     std::string err;
     // precoder store (slots)
     int cap = 0;

@@ -32,6 +32,7 @@ struct KParams;
 cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream);
 cudaError_t launch_tc(int prec, bool held, const KParams &p, int n_cta, cudaStream_t stream);
 int simt_smem_bytes();
+int simt_resident_ctas();
 int tc_smem_bytes(int prec, bool held);
 cudaError_t configure_simt();
 cudaError_t configure_tc();

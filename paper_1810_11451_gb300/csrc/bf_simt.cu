@@ -20,9 +20,19 @@
 
 namespace bfi {
 
-constexpr int SIMT_CWARPS = 8;                         // compute warps
+// Antennas per compute warp (8 or 16) and S ring stages; compile-time knobs.
+#ifndef BF_SIMT_RPW
+#define BF_SIMT_RPW 8
+#endif
+#ifndef BF_SIMT_NS
+#define BF_SIMT_NS 3
+#endif
+constexpr int SIMT_RPW = BF_SIMT_RPW;
+static_assert(SIMT_RPW == 8 || SIMT_RPW == 16, "rows per warp");
+constexpr int SIMT_CWARPS = N_ANT / SIMT_RPW;          // compute warps
 constexpr int SIMT_THREADS = (SIMT_CWARPS + 1) * 32;   // + one producer warp
-constexpr int SIMT_NS = 2;                             // S ring stages
+constexpr int SIMT_MIN_CTAS = SIMT_RPW == 8 ? 2 : 3;   // resident CTAs per SM the registers allow
+constexpr int SIMT_NS = BF_SIMT_NS;                    // S ring stages
 constexpr int SIMT_NW = 2;                             // W buffers
 constexpr int SIMT_S_STAGE = F_LIMIT * S_BYTES_PER_F;  // 17,280 B
 constexpr int SIMT_OFF_S = SIMT_NW * SIMT_IMG_MAX;
@@ -30,7 +40,7 @@ constexpr int SIMT_OFF_BAR = SIMT_OFF_S + SIMT_NS * SIMT_S_STAGE;
 constexpr int SIMT_NBARS = 2 * SIMT_NS + 2 * SIMT_NW;
 constexpr int SIMT_SMEM = SIMT_OFF_BAR + SIMT_NBARS * 8 + 16;
 
-__global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
+__global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SIMT_OFF_BAR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + SIMT_NBARS);
@@ -103,7 +113,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
         }
     } else {
         // ---------------- compute warps ----------------
-        const int i0 = warp * 8;            // first antenna of this warp
+        const int i0 = warp * SIMT_RPW;     // first antenna of this warp
         const int jl = lane < 30 ? lane : 29;  // lanes 30, 31 mirror lane 29 and store nothing
         int nS = 0, nW = 0, wb = 0;
         bool ok = true;
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
                     for (int b = 0; b < tl.nblk; ++b) {
                         uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
 #pragma unroll
-                        for (int r = 0; r < 8; ++r)
+                        for (int r = 0; r < SIMT_RPW; ++r)
                             *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
                                 make_float4(0.f, 0.f, 0.f, 0.f);
                     }
@@ -140,20 +150,22 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
                     break;
                 }
                 const float *Sb = reinterpret_cast<const float *>(smem + SIMT_OFF_S + st * SIMT_S_STAGE);
-                float ar[8][2], ai[8][2];
+                float ar[SIMT_RPW][2], ai[SIMT_RPW][2];
 #pragma unroll
-                for (int r = 0; r < 8; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
+                for (int r = 0; r < SIMT_RPW; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
 #pragma unroll 2
                 for (int k = 0; k < f; ++k) {
                     const float4 s = *reinterpret_cast<const float4 *>(Sb + k * (2 * B_RE) + 4 * jl);
-                    const float4 w0 = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0);
-                    const float4 w1 = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0 + 4);
-                    const float4 v0 = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0);
-                    const float4 v1 = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0 + 4);
-                    const float wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                    const float wi[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    float wr[SIMT_RPW], wi[SIMT_RPW];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) {
+                    for (int q = 0; q < SIMT_RPW / 4; ++q) {  // broadcast loads of the warp's antennas
+                        const float4 w = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0 + 4 * q);
+                        const float4 v = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0 + 4 * q);
+                        wr[4 * q] = w.x, wr[4 * q + 1] = w.y, wr[4 * q + 2] = w.z, wr[4 * q + 3] = w.w;
+                        wi[4 * q] = v.x, wi[4 * q + 1] = v.y, wi[4 * q + 2] = v.z, wi[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < SIMT_RPW; ++r) {
                         ar[r][0] = fmaf(wr[r], s.x, ar[r][0]);
                         ar[r][0] = fmaf(-wi[r], s.y, ar[r][0]);
                         ai[r][0] = fmaf(wr[r], s.y, ai[r][0]);
@@ -170,7 +182,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) bf_simt_kernel(KParams p) {
                 if (lane < 30) {
                     uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
 #pragma unroll
-                    for (int r = 0; r < 8; ++r)
+                    for (int r = 0; r < SIMT_RPW; ++r)
                         *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
                             make_float4(ar[r][0], ai[r][0], ar[r][1], ai[r][1]);
                 }
@@ -205,5 +217,16 @@ cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream) {
 }
 
 int simt_smem_bytes() { return SIMT_SMEM; }
+
+// CTAs of the CUDA-core kernel that fit on one SM at once (registers, shared
+// memory, threads); a launch never asks for more than this many per SM.
+int simt_resident_ctas() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bf_simt_kernel, SIMT_THREADS, SIMT_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
 
 }  // namespace bfi
