@@ -355,6 +355,59 @@ def reduced_leg(torch, bf, plan, batch, ref_d, stream, steps=50):
     return out
 
 
+def fused_output_leg(torch, bf, plan, batch, ref, stream, steps=2000, n_sets=4):
+    """The full-band product writing R straight into the per-antenna layout
+    the OFDM stage reads (antenna i's 3,822 x 60 resource elements in one
+    row), as complex64 or bf16, from complex64 S or held bf16 S. n_sets
+    rotating buffer sets keep the smallest form's working set above L2."""
+    from bfrun import decode_r, layout, rl_layout, set_precoders, to_device_c64
+    set_precoders(plan, batch, torch)
+    lay = layout(batch)
+    lh = layout(batch, 0, bf.BF_BF16)
+    Sflat, _ = batch.pack_S()
+    nb = batch.total_blocks
+    S = [to_device_c64(Sflat, torch) for _ in range(n_sets)]
+    Sq = [torch.empty(lh.held_bytes // 4 + 4, dtype=torch.float32, device="cuda") for _ in range(n_sets)]
+    sc = [torch.empty(nb, dtype=torch.float32, device="cuda") for _ in range(n_sets)]
+    g_c, _ = bf.make_groups(lay.groups)
+    for s in range(n_sets):
+        bf.bf_quantize_symbols(plan, S[s], g_c, bf.BF_BF16, Sq[s], lh.held_off, sc[s], stream)
+    ref_blocks = None if ref is None else ref.reshape(nb, 64, 60)
+    w_bytes = len(set(batch.prec)) * 64 * 36 * 8
+    out = {"blocks": nb, "layout": "antenna-major: row i = antenna i, 60 resource elements per block, blocks in order"}
+    for name, prec, held, rtype in (("bf16x3_c64S_c64R", bf.BF_BF16X3, False, bf.BF_R_C64),
+                                    ("bf16x3_c64S_bf16R", bf.BF_BF16X3, False, bf.BF_R_BF16),
+                                    ("bf16_heldS_bf16R", bf.BF_BF16, True, bf.BF_R_BF16)):
+        rl, offs, nbytes = rl_layout(batch, rtype)
+        R = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(n_sets)]
+        hs = []
+        for s in range(n_sets):
+            so = lh.held_off if held else [g[2] for g in lay.groups]
+            groups = [(g[0], g[1], so[i], offs[i]) for i, g in enumerate(lay.groups)]
+            hs.append(bf.bf_batch_create_rl(plan, Sq[s] if held else S[s], sc[s] if held else None, groups, prec,
+                                            R[s], rl))
+        ms = time_launches(torch, bf, hs, steps, 20, stream) / steps
+        bf.bf_batch_launch(hs[0], stream)
+        torch.cuda.synchronize()
+        err = None
+        if ref_blocks is not None:
+            buf = R[0].cpu().numpy()
+            if rtype == bf.BF_R_C64:
+                got = buf.view(np.complex64).reshape(64, nb, 60).transpose(1, 0, 2).astype(np.complex128)
+            else:
+                got = decode_r(buf.view(np.uint16).reshape(64, nb, 60, 2), rtype).transpose(1, 0, 2)
+            err = float(np.linalg.norm(got - ref_blocks) / np.linalg.norm(ref_blocks))
+        moved = (lh.held_bytes if held else lay.s_bytes) + nbytes + w_bytes
+        out[name] = {"kernel_ms": ms, "gflops": batch.flops() / ms / 1e6, "blocks_per_s": nb / ms * 1e3,
+                     "moved_bytes": int(moved), "moved_gbs": moved / ms / 1e6, "rel_err": err}
+        for h in hs:
+            bf.bf_batch_destroy(h)
+        del R
+    del S, Sq, sc
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_leg(torch, bf, ttis, prec):
     """Continuous-batching serving of 8 cells in real time (0.5 ms TTIs)."""
     import workloads as wl
@@ -436,14 +489,15 @@ def main():
         e2e = end_to_end(torch, bf, plan, Sflat, lay, R_sets[0].numel(), stream, dist, world, flops)
 
     # ---- CPU baseline (oracle), which also gives the references for accuracy
-    cpu, acc, refs = None, None, {}
+    cpu, acc, refs, ref_full = None, None, {}, None
     extra = not args.no_extra and rank == 0
     b_uneven = wl.config_uneven() if extra else None
     b_reduced = wl.config_reduced() if extra else None
     if rank == 0 and not args.no_cpu:
         cpu, ref = cpu_baseline(batch)
         refs = cpu_references({"fullband": ref}, {"uneven": b_uneven, "reduced": b_reduced})
-        Rref_d = to_device_ref(torch, refs.pop("fullband"))
+        ref_full = refs.pop("fullband")
+        Rref_d = to_device_ref(torch, ref_full)
         acc = {}
         for name, h in (("bf16x3", best[0]), ("fp32", plain[0])):
             bf.bf_batch_launch(h, stream)
@@ -459,6 +513,8 @@ def main():
     # ---- the other workloads: uneven batching, reduced precision, serving
     legs = {}
     if extra:
+        legs["fused_output"] = fused_output_leg(torch, bf, plan, batch, ref_full, stream)
+        ref_full = None
         ref_d = to_device_ref(torch, refs.pop("uneven", None))
         legs["uneven"] = uneven_leg(torch, bf, plan, b_uneven, ref_d, stream)
         del ref_d

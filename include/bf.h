@@ -49,7 +49,8 @@ typedef enum {
     BF_ENOTFOUND = 9   /* unknown ticket / unset precoder slot                  */
 } bf_status;
 
-/* Arithmetic of the product. All forms accumulate in FP32 and write complex64 R.
+/* Arithmetic of the product. All forms accumulate in FP32 and write complex64 R
+ * (or the type a bf_rlayout names).
  *  BF_FP32   : plain form, FP32 fused multiply-add on the CUDA cores; S complex64.
  *  BF_BF16   : single-pass tensor-core form, operands rounded to bfloat16.
  *  BF_FP16   : single-pass tensor-core form, operands rounded to binary16.
@@ -163,6 +164,37 @@ bf_status bf_apply_batch(bf_plan plan, const void *S_dev, const float *scale_dev
                          const bf_group *groups, int32_t n_groups, bf_precision prec,
                          void *R_dev, void *stream);
 
+/* Output layout and type of R. The stage after beamforming works per antenna
+ * (each antenna's OFDM modulator takes that antenna's subcarriers as one
+ * vector, Sec. II-III), so R can be written straight into such a layout
+ * instead of block-major complex64. Element (block n of a group, antenna i,
+ * resource element j) is stored at byte
+ *     r_off + n*block_stride + i*row_stride + j*esize
+ * of R_dev, where r_off is the group's offset and esize is 8 for BF_R_C64
+ * (interleaved FP32) and 4 for BF_R_BF16 / BF_R_FP16 (an interleaved pair of
+ * 16-bit values, each rounded to nearest even from the FP32 accumulator).
+ * The packed default (layout == NULL) is {480, 30720, BF_R_C64}.
+ * Antenna-major, subcarrier-contiguous output of T blocks, say, uses
+ *     row_stride = T*60*esize, block_stride = 60*esize,
+ *     r_off of a group = (index of its first block)*60*esize,
+ * so antenna i's T*60 resource elements are one contiguous row.
+ * Rules (BF_EINVAL otherwise): both strides positive multiples of 16, each at
+ * least 60*esize. The caller sizes R_dev and guarantees that no two listed
+ * elements share an address (not checked). */
+typedef enum { BF_R_C64 = 0, BF_R_BF16 = 1, BF_R_FP16 = 2 } bf_rtype;
+typedef struct {
+    int64_t row_stride;    /* bytes between antennas i and i+1 of one block */
+    int64_t block_stride;  /* bytes between blocks n and n+1 of one group   */
+    int32_t rtype;         /* bf_rtype                                      */
+    int32_t reserved;      /* must be 0                                     */
+} bf_rlayout;
+
+/* bf_apply_batch with an explicit R layout (NULL = the packed default). The
+ * product and its FP32 accumulation are unchanged; only the store differs. */
+bf_status bf_apply_batch_rl(bf_plan plan, const void *S_dev, const float *scale_dev,
+                            const bf_group *groups, int32_t n_groups, bf_precision prec,
+                            void *R_dev, const bf_rlayout *layout, void *stream);
+
 /* The same product with S and R in HOST memory (best pinned). S is copied in,
  * the product runs, R is copied out, pipelined in chunks of groups over two
  * internal streams so that copies overlap the kernels. Ordered after
@@ -184,6 +216,10 @@ typedef struct bf_batch_s *bf_batch;
 bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev,
                           const bf_group *groups, int32_t n_groups, bf_precision prec,
                           void *R_dev, bf_batch *out);
+/* bf_batch_create with an explicit R layout (as bf_apply_batch_rl). */
+bf_status bf_batch_create_rl(bf_plan plan, const void *S_dev, const float *scale_dev,
+                             const bf_group *groups, int32_t n_groups, bf_precision prec,
+                             void *R_dev, const bf_rlayout *layout, bf_batch *out);
 bf_status bf_batch_launch(bf_batch batch, void *stream);
 bf_status bf_batch_launch_graph(bf_batch batch, void *stream);
 bf_status bf_batch_destroy(bf_batch batch);

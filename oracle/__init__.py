@@ -154,6 +154,11 @@ def fp16_round(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
 
 
+def fp16_bits(x: np.ndarray) -> np.ndarray:
+    """The 16-bit patterns of fp16_round(x)."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).view(np.uint16)
+
+
 def split_bf16(x: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     """x ~ hi + lo with hi = bf16(x) and lo = bf16(x - hi); x - hi is exact in FP32."""
     x = np.asarray(x, dtype=np.float32)

@@ -30,11 +30,28 @@ PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "fp16": BF_FP16, "bf16x3": BF_BF
 N_ANT, B_RE, F_LIMIT = 64, 60, 36
 S_BYTES_PER_F = B_RE * 8      # one flow row of a complex64 S block
 R_BLOCK_BYTES = N_ANT * B_RE * 8
+# bf_rtype: element type of R
+BF_R_C64, BF_R_BF16, BF_R_FP16 = range(3)
+R_ESIZE = {BF_R_C64: 8, BF_R_BF16: 4, BF_R_FP16: 4}
 
 
 class bf_group(ctypes.Structure):
     """One group of blocks sharing precoder `prec_id` (byte offsets)."""
     _fields_ = [("prec_id", c_int32), ("n_blocks", c_int32), ("s_off", c_int64), ("r_off", c_int64)]
+
+
+class bf_rlayout(ctypes.Structure):
+    """Output layout of R: element (block n, antenna i, RE j) of a group at byte
+    r_off + n*block_stride + i*row_stride + j*esize, in type `rtype`."""
+    _fields_ = [("row_stride", c_int64), ("block_stride", c_int64), ("rtype", c_int32), ("reserved", c_int32)]
+
+
+def antenna_major_layout(total_blocks: int, rtype: int = BF_R_C64) -> bf_rlayout:
+    """The layout in which antenna i's total_blocks*60 resource elements form
+    one contiguous row (block n of the batch at column n*60); a group whose
+    first block has batch index n0 takes r_off = n0*60*esize."""
+    e = R_ESIZE[int(rtype)]
+    return bf_rlayout(int(total_blocks) * B_RE * e, B_RE * e, int(rtype), 0)
 
 
 class BfError(RuntimeError):
@@ -69,6 +86,10 @@ def lib() -> ctypes.CDLL:
                                             c_void_p]),
             "bf_batch_create": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
                                         POINTER(c_void_p)]),
+            "bf_apply_batch_rl": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
+                                          POINTER(bf_rlayout), c_void_p]),
+            "bf_batch_create_rl": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int,
+                                           c_void_p, POINTER(bf_rlayout), POINTER(c_void_p)]),
             "bf_batch_launch": (c_int, [c_void_p, c_void_p]),
             "bf_batch_destroy": (c_int, [c_void_p]),
             "bf_errnorm": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
@@ -194,6 +215,14 @@ def bf_apply_batch(plan, S_dev, scale_dev, groups, prec: int, R_dev, stream=None
                                 _stream(stream)), plan)
 
 
+def bf_apply_batch_rl(plan, S_dev, scale_dev, groups, prec: int, R_dev, layout: Optional[bf_rlayout],
+                      stream=None) -> None:
+    ga, n = make_groups(groups)
+    lp = ctypes.byref(layout) if layout is not None else None
+    _check(lib().bf_apply_batch_rl(plan, _ptr(S_dev), _ptr(scale_dev), ga, n, int(prec), _ptr(R_dev), lp,
+                                   _stream(stream)), plan)
+
+
 def bf_apply_batch_host(plan, S_host, groups, prec: int, R_host, stream=None) -> None:
     ga, n = make_groups(groups)
     _check(lib().bf_apply_batch_host(plan, _ptr(S_host), ga, n, int(prec), _ptr(R_host), _stream(stream)), plan)
@@ -204,6 +233,15 @@ def bf_batch_create(plan, S_dev, scale_dev, groups, prec: int, R_dev) -> int:
     h = c_void_p()
     _check(lib().bf_batch_create(plan, _ptr(S_dev), _ptr(scale_dev), ga, n, int(prec), _ptr(R_dev),
                                  ctypes.byref(h)), plan)
+    return h.value
+
+
+def bf_batch_create_rl(plan, S_dev, scale_dev, groups, prec: int, R_dev, layout: Optional[bf_rlayout]) -> int:
+    ga, n = make_groups(groups)
+    h = c_void_p()
+    lp = ctypes.byref(layout) if layout is not None else None
+    _check(lib().bf_batch_create_rl(plan, _ptr(S_dev), _ptr(scale_dev), ga, n, int(prec), _ptr(R_dev), lp,
+                                    ctypes.byref(h)), plan)
     return h.value
 
 

@@ -66,6 +66,15 @@ struct KParams {
     int64_t w_tc_stride;
     const float *w_scale;      // per slot: power of two undoing the image scale
     int *status;               // device status word
+    // Output layout: element (block, antenna i, resource element j) of R at
+    // tile.r_off + b*r_block_stride + i*r_row_stride + j*esize, esize 8 for
+    // complex64 and 4 for the 16-bit pairs (r_type 1 = bf16, 2 = fp16).
+    int64_t r_row_stride;
+    int64_t r_block_stride;
+    int32_t r_type;
+    int32_t r_esize;
 };
+
+constexpr int R_C64 = 0, R_BF16 = 1, R_FP16 = 2;
 
 }  // namespace bfi

@@ -341,7 +341,7 @@ extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const 
 // bytes moved before), so each CTA loads a precoder once per range and
 // streams its S blocks.
 void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *groups, int32_t n_groups,
-                    bf_precision prec, bool held, int max_cta, WorkList &wl) {
+                    bf_precision prec, bool held, int max_cta, int64_t r_block_stride, WorkList &wl) {
     // count first, so the arrays are sized once (the buffers persist across
     // calls in the plan, so steady-state scheduling allocates nothing)
     int n_tiles = 0;
@@ -364,7 +364,7 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
         for (int b0 = 0; b0 < gr.n_blocks; b0 += tile_blocks, ++n) {
             Tile &t = tiles[n];
             t.s_off = gr.s_off + (int64_t)b0 * sb;
-            t.r_off = gr.r_off + (int64_t)b0 * R_BLOCK_BYTES;
+            t.r_off = gr.r_off + (int64_t)b0 * r_block_stride;
             t.prec = gr.prec_id;
             t.sblk = blk + b0;
             t.f = (int16_t)f;
@@ -423,7 +423,7 @@ extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const 
     }
     static thread_local WorkList wl;  // reused: repeated calls allocate nothing
     const TuneTable tune;
-    build_worklist(f_of_slot, tune, groups, n_groups, prec, held != 0, max_cta, wl);
+    build_worklist(f_of_slot, tune, groups, n_groups, prec, held != 0, max_cta, R_BLOCK_BYTES, wl);
     const int nt = (int)wl.tiles.size();
     *n_cta_out = (int32_t)wl.cta_begin.size() - 1;
     if (!tiles_out) return nt;  // size query
@@ -457,8 +457,22 @@ static bf_status validate_apply(bf_plan plan, const void *S, const float *scale,
     return check_group_slots(plan, groups, n_groups);
 }
 
+// Element size of R for an output type.
+static int r_esize_of(int32_t rtype) { return rtype == BF_R_C64 ? 8 : 4; }
+static int64_t r_block_stride_of(const bf_rlayout *layout) { return layout ? layout->block_stride : R_BLOCK_BYTES; }
+
+static bf_status validate_rlayout(bf_plan plan, const bf_rlayout *l) {
+    if (!l) return BF_OK;
+    if (l->rtype < BF_R_C64 || l->rtype > BF_R_FP16) return bf_fail(plan, BF_EINVAL, "unknown R type %d", l->rtype);
+    if (l->reserved != 0) return bf_fail(plan, BF_EINVAL, "bf_rlayout.reserved must be 0");
+    const int64_t row_min = (int64_t)B_RE * r_esize_of(l->rtype);
+    if (l->row_stride < row_min || l->block_stride < row_min || (l->row_stride & 15) || (l->block_stride & 15))
+        return bf_fail(plan, BF_EINVAL, "R strides must be multiples of 16 and at least %lld bytes", (long long)row_min);
+    return BF_OK;
+}
+
 static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_bytes, const void *S, const float *scale,
-                           void *R, bf_precision prec) {
+                           void *R, bf_precision prec, const bf_rlayout *layout) {
     KParams p{};
     p.tiles = reinterpret_cast<const Tile *>(dlist);
     p.cta_begin = reinterpret_cast<const int32_t *>(dlist + tiles_bytes);
@@ -470,6 +484,10 @@ static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_byte
     p.w_tc_stride = prec == BF_FP16 ? W_FP16_STRIDE : W_BF16X2_STRIDE;
     p.w_scale = plan->w_scale;
     p.status = plan->d_status;
+    p.r_row_stride = layout ? layout->row_stride : (int64_t)B_RE * 8;
+    p.r_block_stride = r_block_stride_of(layout);
+    p.r_type = layout ? layout->rtype : R_C64;
+    p.r_esize = layout ? r_esize_of(layout->rtype) : 8;
     return p;
 }
 
@@ -486,11 +504,11 @@ cudaError_t launch_kernel(bf_precision prec, bool held, const KParams &p, int n_
 // Upload a work list through the plan's ring (one entry per call in flight)
 // and launch it. `max_cta` <= 0 means the tuned default.
 bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const bf_group *groups, int32_t n_groups,
-                        bf_precision prec, void *R, cudaStream_t st, int max_cta) {
+                        bf_precision prec, void *R, cudaStream_t st, int max_cta, const bf_rlayout *layout) {
     const bool held = scale != nullptr;
     WorkList &wl = plan->scratch_wl;
     build_worklist(plan->f_slot.data(), plan->tune, groups, n_groups, prec, held,
-                   max_cta > 0 ? max_cta : max_cta_for(plan, prec), wl);
+                   max_cta > 0 ? max_cta : max_cta_for(plan, prec), r_block_stride_of(layout), wl);
     if (wl.tiles.empty()) return BF_OK;
     bf_status s;
     const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
@@ -521,19 +539,26 @@ bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const b
         // the cached device copy may be in use on another stream: order after it
         BF_CK(plan, cudaStreamWaitEvent(st, hit->ev, 0));
     }
-    const KParams p = make_params(plan, hit->d, tb, S, scale, R, prec);
+    const KParams p = make_params(plan, hit->d, tb, S, scale, R, prec, layout);
     BF_CK(plan, launch_kernel(prec, held, p, (int)wl.cta_begin.size() - 1, st));
     BF_CK(plan, cudaEventRecord(hit->ev, st));
     plan->launches++;
     return BF_OK;
 }
 
-extern "C" bf_status bf_apply_batch(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
-                                    int32_t n_groups, bf_precision prec, void *R_dev, void *stream) {
+extern "C" bf_status bf_apply_batch_rl(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
+                                       int32_t n_groups, bf_precision prec, void *R_dev, const bf_rlayout *layout,
+                                       void *stream) {
     bf_status s = validate_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, true);
+    if (s == BF_OK) s = validate_rlayout(plan, layout);
     if (s != BF_OK || n_groups == 0) return s;
     if ((s = plan_ensure_device(plan)) != BF_OK) return s;
-    return enqueue_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, (cudaStream_t)stream, 0);
+    return enqueue_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, (cudaStream_t)stream, 0, layout);
+}
+
+extern "C" bf_status bf_apply_batch(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
+                                    int32_t n_groups, bf_precision prec, void *R_dev, void *stream) {
+    return bf_apply_batch_rl(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, nullptr, stream);
 }
 
 // ------------------------------------------------------------------ prepared batches
@@ -548,16 +573,18 @@ struct bf_batch_s {
     bool held = false;
 };
 
-extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
-                                     int32_t n_groups, bf_precision prec, void *R_dev, bf_batch *out) {
+extern "C" bf_status bf_batch_create_rl(bf_plan plan, const void *S_dev, const float *scale_dev,
+                                        const bf_group *groups, int32_t n_groups, bf_precision prec, void *R_dev,
+                                        const bf_rlayout *layout, bf_batch *out) {
     if (!out) return bf_fail(plan, BF_EINVAL, "out is NULL");
     *out = nullptr;
     bf_status s = validate_apply(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, true);
+    if (s == BF_OK) s = validate_rlayout(plan, layout);
     if (s != BF_OK) return s;
     if ((s = plan_ensure_device(plan)) != BF_OK) return s;
     WorkList wl;
     build_worklist(plan->f_slot.data(), plan->tune, groups, n_groups, prec, scale_dev != nullptr,
-                   max_cta_for(plan, prec), wl);
+                   max_cta_for(plan, prec), r_block_stride_of(layout), wl);
     bf_batch bt = new bf_batch_s();
     bt->plan = plan;
     const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
@@ -574,7 +601,7 @@ extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const floa
             return bf_fail(plan, BF_ECUDA, "work-list upload: %s", cudaGetErrorString(e));
         }
     }
-    bt->p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec);
+    bt->p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec, layout);
     bt->n_cta = wl.tiles.empty() ? 0 : (int)wl.cta_begin.size() - 1;
     bt->prec = prec;
     bt->held = scale_dev != nullptr;
@@ -593,6 +620,11 @@ extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const floa
     }
     *out = bt;
     return BF_OK;
+}
+
+extern "C" bf_status bf_batch_create(bf_plan plan, const void *S_dev, const float *scale_dev, const bf_group *groups,
+                                     int32_t n_groups, bf_precision prec, void *R_dev, bf_batch *out) {
+    return bf_batch_create_rl(plan, S_dev, scale_dev, groups, n_groups, prec, R_dev, nullptr, out);
 }
 
 extern "C" bf_status bf_batch_launch(bf_batch batch, void *stream) {

@@ -97,8 +97,9 @@ struct bf_plan_s {
 bf_status bf_fail(bf_plan plan, bf_status s, const char *fmt, ...);
 bf_status plan_ensure_device(bf_plan plan);
 void build_worklist(const int *f_slot, const bfi::TuneTable &tune, const bf_group *groups, int32_t n_groups,
-                    bf_precision prec, bool held, int max_cta, bfi::WorkList &wl);
+                    bf_precision prec, bool held, int max_cta, int64_t r_block_stride, bfi::WorkList &wl);
+// `layout` nullptr = packed block-major complex64 R; otherwise already validated.
 bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const bf_group *groups, int32_t n_groups,
-                        bf_precision prec, void *R, cudaStream_t st, int max_cta);
+                        bf_precision prec, void *R, cudaStream_t st, int max_cta, const bf_rlayout *layout = nullptr);
 int max_cta_for(bf_plan plan, bf_precision prec);
 cudaError_t launch_kernel(bf_precision prec, bool held, const bfi::KParams &p, int n_cta, cudaStream_t st);

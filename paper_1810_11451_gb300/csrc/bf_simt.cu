@@ -13,12 +13,30 @@
 // and 31 idle). Per flow k a lane reads its two S values with one 16-byte
 // shared load and the warp's 8+8 W values as broadcasts, then issues 64 FFMA.
 // R rows are written with 16-byte stores, 480 contiguous bytes per warp.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "bf_device.cuh"
 #include "bf_internal.h"
 
 namespace bfi {
+
+// Two consecutive elements of one antenna row of R in the output type:
+// complex64 (16 bytes) or bf16 / fp16 pairs rounded to nearest even (8 bytes).
+__device__ __forceinline__ void store_r2(uint8_t *dst, float re0, float im0, float re1, float im1, int r_type) {
+    if (r_type == R_C64) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(re0, im0, re1, im1);
+    } else if (r_type == R_BF16) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(re0, im0), b = __floats2bfloat162_rn(re1, im1);
+        *reinterpret_cast<uint2 *>(dst) =
+            make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+    } else {
+        __half2 a = __floats2half2_rn(re0, im0), b = __floats2half2_rn(re1, im1);
+        *reinterpret_cast<uint2 *>(dst) =
+            make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+    }
+}
 
 // Antennas per compute warp (8 or 16) and S ring stages; compile-time knobs.
 #ifndef BF_SIMT_RPW
@@ -124,11 +142,11 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                 // empty sum: R = 0
                 if (lane < 30) {
                     for (int b = 0; b < tl.nblk; ++b) {
-                        uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
+                        uint8_t *rb = p.R + tl.r_off + (int64_t)b * p.r_block_stride;
 #pragma unroll
                         for (int r = 0; r < SIMT_RPW; ++r)
-                            *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
-                                make_float4(0.f, 0.f, 0.f, 0.f);
+                            store_r2(rb + (i0 + r) * p.r_row_stride + lane * 2 * p.r_esize, 0.f, 0.f, 0.f, 0.f,
+                                     p.r_type);
                     }
                 }
                 continue;
@@ -180,11 +198,11 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                 if (lane == 0) bfd::mbar_arrive(s_empty(st));
                 ++nS;
                 if (lane < 30) {
-                    uint8_t *rb = p.R + tl.r_off + (int64_t)b * R_BLOCK_BYTES;
+                    uint8_t *rb = p.R + tl.r_off + (int64_t)b * p.r_block_stride;
 #pragma unroll
                     for (int r = 0; r < SIMT_RPW; ++r)
-                        *reinterpret_cast<float4 *>(rb + (i0 + r) * (B_RE * 8) + lane * 16) =
-                            make_float4(ar[r][0], ai[r][0], ar[r][1], ai[r][1]);
+                        store_r2(rb + (i0 + r) * p.r_row_stride + lane * 2 * p.r_esize, ar[r][0], ai[r][0], ar[r][1],
+                                 ai[r][1], p.r_type);
                 }
             }
             if (ok && (tl.flags & TF_LAST_OF_W)) {

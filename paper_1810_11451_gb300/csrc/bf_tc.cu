@@ -112,6 +112,14 @@ __device__ __forceinline__ float2 unpack2_bf16(uint32_t u) {
     return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
 }
 
+// One element (re, im) of R in the output type: complex64, or a bf16 / fp16
+// pair rounded to nearest even.
+__device__ __forceinline__ void store_r(uint8_t *dst, float re, float im, int r_type) {
+    if (r_type == R_C64) *reinterpret_cast<float2 *>(dst) = make_float2(re, im);
+    else if (r_type == R_BF16) *reinterpret_cast<uint32_t *>(dst) = pack2_bf16(re, im);
+    else *reinterpret_cast<uint32_t *>(dst) = pack2_fp16(re, im);
+}
+
 template <int TERMS, bool HELD, bool BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     using C = TcCfg<TERMS, HELD>;
@@ -350,13 +358,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
         constexpr int NCH = 4 / (TC_EPI_WARPS / 4);   // 32-column chunks per warp
         const int c0 = ((warp - TC_EPI0) >> 2) * NCH; // first chunk of this warp
         int n = 0;
+        const int64_t rs = p.r_row_stride;
         for (int t = t0; t < t1; ++t) {
             const Tile tl = p.tiles[t];
             const bool live = blk < tl.nblk && j < B_RE;
-            float2 *rrow = reinterpret_cast<float2 *>(p.R + tl.r_off + (int64_t)blk * R_BLOCK_BYTES) + j;
+            // this lane's element of antenna 0; antenna i is rs bytes further
+            uint8_t *rj = p.R + tl.r_off + (int64_t)blk * p.r_block_stride + (int64_t)j * p.r_esize;
             if (tl.f == 0) {
                 if (live)
-                    for (int i = 16 * c0; i < 16 * (c0 + NCH); ++i) rrow[i * B_RE] = make_float2(0.f, 0.f);
+                    for (int i = 16 * c0; i < 16 * (c0 + NCH); ++i) store_r(rj + i * rs, 0.f, 0.f, p.r_type);
                 continue;
             }
             const int d = n % TC_NACC;
@@ -371,10 +381,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 bfd::tmem_ld32(ta + 32 * c, v);
                 bfd::tmem_ld_wait();
                 if (live) {
+                    if (p.r_type == R_C64) {
 #pragma unroll
-                    for (int u = 0; u < 16; ++u)
-                        rrow[(16 * c + u) * B_RE] =
-                            make_float2(__uint_as_float(v[2 * u]) * scale, __uint_as_float(v[2 * u + 1]) * scale);
+                        for (int u = 0; u < 16; ++u)
+                            *reinterpret_cast<float2 *>(rj + (16 * c + u) * rs) = make_float2(
+                                __uint_as_float(v[2 * u]) * scale, __uint_as_float(v[2 * u + 1]) * scale);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            store_r(rj + (16 * c + u) * rs, __uint_as_float(v[2 * u]) * scale,
+                                    __uint_as_float(v[2 * u + 1]) * scale, p.r_type);
+                    }
                 }
             }
             bfd::tc_fence_before();

@@ -105,3 +105,81 @@ def run(plan, batch, prec: int, torch, held: bool = False, mode: str = "apply", 
     if return_buffers:
         return out, dict(S=S_use, scale=scale, R=R_t, groups=groups, S_c64=S_d)
     return out
+
+
+def rl_layout(batch, rtype: int, pad_block: int = 0, pad_row: int = 0):
+    """An antenna-major R layout over the whole batch (antenna i's resource
+    elements of every block in one row), with optional padding bytes after
+    each block's row segment and after each antenna row. Returns
+    (bf_rlayout, group r_off list, total bytes)."""
+    e = bf.R_ESIZE[rtype]
+    bs = B_RE * e + pad_block
+    T = batch.total_blocks
+    rs = max(1, T) * bs + pad_row
+    offs, n0 = [], 0
+    for nb in batch.n_blocks:
+        offs.append(n0 * bs)
+        n0 += nb
+    return bf.bf_rlayout(rs, bs, rtype, 0), offs, N_ANT * rs
+
+
+def run_rl(plan, batch, prec: int, torch, rtype: int, held: bool = False, pad_block: int = 0, pad_row: int = 0,
+           mode: str = "apply", set_w: bool = True):
+    """bf_apply_batch_rl (or a prepared batch) into an antenna-major R.
+    Returns (R bytes as a numpy uint8 array, bf_rlayout, group r_off list).
+    The R buffer is filled with 0xFF bytes first (NaN in every R type)."""
+    if set_w:
+        set_precoders(plan, batch, torch)
+    lay = layout(batch, 0, prec)
+    rl, offs, nbytes = rl_layout(batch, rtype, pad_block, pad_row)
+    Sflat, _ = batch.pack_S()
+    S_d = to_device_c64(Sflat, torch)
+    scale, S_use = None, S_d
+    s_offs = [g[2] for g in lay.groups]
+    if held:
+        Sq = torch.zeros(max(16, lay.held_bytes) // 4 + 4, dtype=torch.float32, device="cuda")
+        scale = torch.zeros(max(1, batch.total_blocks), dtype=torch.float32, device="cuda")
+        bf.bf_quantize_symbols(plan, S_d, lay.groups, prec, Sq, lay.held_off, scale)
+        S_use, s_offs = Sq, lay.held_off
+    groups = [(g[0], g[1], s_offs[i], offs[i]) for i, g in enumerate(lay.groups)]
+    R_t = torch.full((max(16, nbytes),), 255, dtype=torch.uint8, device="cuda")
+    if mode == "apply":
+        bf.bf_apply_batch_rl(plan, S_use, scale, groups, prec, R_t, rl)
+    elif mode in ("batch", "graph"):
+        h = bf.bf_batch_create_rl(plan, S_use, scale, groups, prec, R_t, rl)
+        (bf.bf_batch_launch if mode == "batch" else bf.bf_batch_launch_graph)(h)
+        torch.cuda.synchronize()
+        bf.bf_batch_destroy(h)
+    else:
+        raise ValueError(mode)
+    torch.cuda.synchronize()
+    return R_t.cpu().numpy(), rl, offs
+
+
+def rl_view(buf: np.ndarray, rl, r_off: int, n_blocks: int) -> np.ndarray:
+    """Group view of an R buffer in layout rl: complex64 (n_blocks, 64, 60) for
+    BF_R_C64, else uint16 (n_blocks, 64, 60, 2) holding the (re, im) bit patterns."""
+    if rl.rtype == bf.BF_R_C64:
+        return np.ndarray((n_blocks, N_ANT, B_RE), np.complex64, buf, r_off, (rl.block_stride, rl.row_stride, 8))
+    return np.ndarray((n_blocks, N_ANT, B_RE, 2), np.uint16, buf, r_off, (rl.block_stride, rl.row_stride, 4, 2))
+
+
+def decode_r(v: np.ndarray, rtype: int) -> np.ndarray:
+    """Elements read through rl_view (or any (..., 2) uint16 pair array for the
+    16-bit types) as complex128 values."""
+    if rtype == bf.BF_R_C64:
+        return v.astype(np.complex128)
+    if rtype == bf.BF_R_BF16:
+        f = (v.astype(np.uint32) << np.uint32(16)).view(np.float32)
+    else:
+        f = np.ascontiguousarray(v).view(np.float16).astype(np.float32)
+    return f[..., 0].astype(np.float64) + 1j * f[..., 1].astype(np.float64)
+
+
+def rl_written_mask(nbytes: int, rl, offs, n_blocks) -> np.ndarray:
+    """Bytes of an R buffer that layout rl assigns to some element."""
+    m = np.zeros(max(16, nbytes), np.bool_)
+    e = bf.R_ESIZE[rl.rtype]
+    for o, nb in zip(offs, n_blocks):
+        np.ndarray((nb, N_ANT, B_RE, e), np.bool_, m, o, (rl.block_stride, rl.row_stride, e, 1))[...] = True
+    return m

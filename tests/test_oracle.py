@@ -263,6 +263,25 @@ def test_fp16_round_matches_library():
     assert np.array_equal(oracle.fp16_round(x).view(np.uint32), ref.view(np.uint32))
 
 
+# binary16: 1 sign, 5 exponent (bias 15), 10 fraction bits
+FP16_CASES = [
+    (1.0, 0x3C00),
+    (-2.0, 0xC000),
+    (65504.0, 0x7BFF),     # largest finite
+    (2049.0, 0x6800),      # tie between 2048 and 2050: even mantissa (2048)
+    (2051.0, 0x6802),      # tie between 2050 and 2052: even mantissa (2052)
+    (2050.0, 0x6801),      # exact
+    (0.0, 0x0000),
+    (-0.0, 0x8000),
+    (2.0 ** -24, 0x0001),  # smallest subnormal
+]
+
+
+def test_fp16_bits_cases():
+    x = np.array([c[0] for c in FP16_CASES], dtype=np.float32)
+    assert [int(g) for g in oracle.fp16_bits(x)] == [c[1] for c in FP16_CASES]
+
+
 def test_split_bf16_bound():
     """hi + lo reproduces x to 2^-16 relative; both parts are bf16 values."""
     rng = np.random.default_rng(23)
