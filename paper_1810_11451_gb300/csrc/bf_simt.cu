@@ -83,17 +83,21 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
         bfd::mbar_init_fence();
     }
     __syncthreads();
-    // No global memory touched yet: let the next launch start its prologue,
-    // then wait for the previous kernel on the stream to finish.
+    // No global memory touched yet: let the next launch start its prologue.
+    // The compute warps (which write R) wait for the previous kernel on the
+    // stream to finish before anything else; the producer waits just before
+    // its first S copy, so its first precoder image loads while the previous
+    // grid drains (precoder images and work lists are never written by a grid
+    // with early release: both are complete before this grid can start).
     bfd::grid_dep_launch();
-    bfd::grid_dep_wait();
+    if (warp != SIMT_CWARPS) bfd::grid_dep_wait();
     const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == SIMT_CWARPS) {
         // ---------------- producer ----------------
         if (lane == 0) {
             int nS = 0, nW = 0;
-            bool ok = true;
+            bool ok = true, dep_done = false;
             for (int t = t0; t < t1 && ok; ++t) {
                 const Tile tl = p.tiles[t];
                 if (tl.f == 0) continue;
@@ -108,6 +112,10 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                     bfd::bulk_g2s(bfd::smem_u32(smem + wb * SIMT_IMG_MAX),
                                   p.w_simt + (int64_t)tl.prec * W_SIMT_STRIDE, bytes, w_full(wb));
                     ++nW;
+                }
+                if (!dep_done) {
+                    bfd::grid_dep_wait();
+                    dep_done = true;
                 }
                 const uint32_t bytes = (uint32_t)(tl.f * S_BYTES_PER_F);
                 for (int b = 0; b < tl.nblk; ++b) {

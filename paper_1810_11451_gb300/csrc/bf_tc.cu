@@ -173,9 +173,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     bfd::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     // The prologue above touched no global memory: let the next launch on the
-    // stream begin its own, then wait for the previous one to finish.
+    // stream begin its own. Then every role but the W producer waits for the
+    // previous grid on the stream to finish (its R may be this grid's S, its S
+    // this grid's R). The W producer reads only precoder images and the work
+    // list, which no grid with early release writes: the precoder kernel
+    // releases its dependents only by completing and work lists are uploaded
+    // by copies, both ordered before this grid could start. So it loads its
+    // first precoder while the previous grid drains.
     bfd::grid_dep_launch();
-    bfd::grid_dep_wait();
+    if (warp != 2) bfd::grid_dep_wait();
     const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == 0) {
