@@ -196,8 +196,10 @@ bf_status bf_apply_batch_rl(bf_plan plan, const void *S_dev, const float *scale_
                             void *R_dev, const bf_rlayout *layout, void *stream);
 
 /* The same product with S and R in HOST memory (best pinned). S is copied in,
- * the product runs, R is copied out, pipelined in chunks of groups over two
- * internal streams so that copies overlap the kernels. Ordered after
+ * the product runs, R is copied out, pipelined in chunks of groups (S + R
+ * of 2 MiB first, doubling up to 32 MiB) over three internal streams (copy
+ * in, compute, copy out), so both directions of the host link stay busy.
+ * Ordered after
  * `stream`; `stream` is ordered after its completion (synchronise `stream`
  * before reading R_host). Group offsets refer to the host buffers. */
 bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups,

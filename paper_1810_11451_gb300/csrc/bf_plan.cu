@@ -142,13 +142,18 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
             return bf_fail(nullptr, BF_ECUDA, "cudaEventCreate failed");
         }
     }
-    if (cudaEventCreateWithFlags(&p->prep_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&p->xfer[0], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&p->xfer[1], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->xfer_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->xfer_ev[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->xfer_ev[2], cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaEventCreateWithFlags(&p->prep_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->x_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->x_run, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->x_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->x_start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->x_end, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < BF_XFER_SLOTS; ++i)
+        ok = cudaEventCreateWithFlags(&p->x_in_done[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->x_run_done[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->x_out_done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         bf_plan_destroy(p);
         return bf_fail(nullptr, BF_ECUDA, "stream/event creation failed");
@@ -168,17 +173,22 @@ extern "C" bf_status bf_plan_destroy(bf_plan plan) {
         if (w.ev) cudaEventDestroy(w.ev);
     }
     void *dev_ptrs[] = {plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_scale, plan->d_status,
-                        plan->prep_d, plan->en_d, plan->x_s[0], plan->x_s[1], plan->x_r[0], plan->x_r[1]};
+                        plan->prep_d, plan->en_d};
     for (void *q : dev_ptrs)
         if (q) cudaFree(q);
+    for (int i = 0; i < BF_XFER_SLOTS; ++i) {
+        if (plan->x_s[i]) cudaFree(plan->x_s[i]);
+        if (plan->x_r[i]) cudaFree(plan->x_r[i]);
+        for (cudaEvent_t e : {plan->x_in_done[i], plan->x_run_done[i], plan->x_out_done[i]})
+            if (e) cudaEventDestroy(e);
+    }
     if (plan->prep_h) cudaFreeHost(plan->prep_h);
     if (plan->en_h) cudaFreeHost(plan->en_h);
     if (plan->prep_ev) cudaEventDestroy(plan->prep_ev);
-    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
-    for (int i = 0; i < 2; ++i)
-        if (plan->xfer[i]) cudaStreamDestroy(plan->xfer[i]);
-    for (int i = 0; i < 3; ++i)
-        if (plan->xfer_ev[i]) cudaEventDestroy(plan->xfer_ev[i]);
+    if (plan->x_start) cudaEventDestroy(plan->x_start);
+    if (plan->x_end) cudaEventDestroy(plan->x_end);
+    for (cudaStream_t st : {plan->cap_stream, plan->x_in, plan->x_run, plan->x_out})
+        if (st) cudaStreamDestroy(st);
     cudaGetLastError();
     delete plan;
     return BF_OK;
@@ -658,16 +668,22 @@ extern "C" bf_status bf_batch_destroy(bf_batch batch) {
 }
 
 // ------------------------------------------------------------------ host buffers
-// Chunks of consecutive groups are copied in, multiplied and copied out on two
-// internal streams, so the copies of one chunk overlap the kernel of another.
+// Chunks of consecutive groups flow through three streams: copy-in (x_in),
+// compute (x_run) and copy-out (x_out), over a ring of BF_XFER_SLOTS device
+// staging slots. Each direction of the host link stays busy on its own
+// stream; a slot's S is reused once the kernel that read it has run, its R
+// once the copy-out that read it has finished.
 extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups, int32_t n_groups,
                                          bf_precision prec, void *R_host, void *stream) {
     bf_status s = validate_apply(plan, S_host, nullptr, groups, n_groups, prec, R_host, false);
     if (s != BF_OK || n_groups == 0) return s;
     if ((s = plan_ensure_device(plan)) != BF_OK) return s;
     cudaStream_t user = (cudaStream_t)stream;
-    // chunking by bytes
-    const int64_t target = plan->host_chunk_bytes;
+    // chunking by bytes (S + R): the first chunk is small so that the
+    // copy-out starts early, later ones double up to host_chunk_bytes (large
+    // enough that issuing a chunk's calls takes less host time than the link
+    // takes to move it)
+    int64_t target = std::min<int64_t>(BF_HOST_CHUNK_FIRST, plan->host_chunk_bytes);
     std::vector<int> cut{0};
     int64_t acc = 0, max_s = 0, max_r = 0, cs = 0, cr = 0;
     for (int g = 0; g < n_groups; ++g) {
@@ -676,6 +692,7 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
         const int64_t rb = (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
         if (acc > 0 && acc + sb + rb > target) {
             cut.push_back(g);
+            target = std::min<int64_t>(2 * target, plan->host_chunk_bytes);
             max_s = std::max(max_s, cs);
             max_r = std::max(max_r, cr);
             acc = cs = cr = 0;
@@ -687,20 +704,24 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
     cut.push_back(n_groups);
     max_s = std::max(max_s, cs);
     max_r = std::max(max_r, cr);
-    for (int i = 0; i < 2; ++i) {
+    const int n_chunks = (int)cut.size() - 1;
+    const int slots = std::min(n_chunks, BF_XFER_SLOTS);
+    for (int i = 0; i < slots; ++i) {
         if ((s = grow_dev(plan, &plan->x_s[i], &plan->x_scap[i], (size_t)std::max<int64_t>(max_s, 16))) != BF_OK) return s;
         if ((s = grow_dev(plan, &plan->x_r[i], &plan->x_rcap[i], (size_t)std::max<int64_t>(max_r, 16))) != BF_OK) return s;
     }
-    BF_CK(plan, cudaEventRecord(plan->xfer_ev[2], user));
-    BF_CK(plan, cudaStreamWaitEvent(plan->xfer[0], plan->xfer_ev[2], 0));
-    BF_CK(plan, cudaStreamWaitEvent(plan->xfer[1], plan->xfer_ev[2], 0));
+    BF_CK(plan, cudaEventRecord(plan->x_start, user));
+    BF_CK(plan, cudaStreamWaitEvent(plan->x_in, plan->x_start, 0));
+    BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_start, 0));
+    BF_CK(plan, cudaStreamWaitEvent(plan->x_out, plan->x_start, 0));
     std::vector<bf_group> local;
-    for (size_t c = 0; c + 1 < cut.size(); ++c) {
-        const int i = (int)(c & 1);
-        cudaStream_t st = plan->xfer[i];
+    for (int c = 0; c < n_chunks; ++c) {
+        const int k = c % BF_XFER_SLOTS;
+        const bool reuse = c >= BF_XFER_SLOTS;
+        // copy S in, merging groups that are contiguous in the host buffer
+        if (reuse) BF_CK(plan, cudaStreamWaitEvent(plan->x_in, plan->x_run_done[k], 0));
         local.clear();
         int64_t so = 0, ro = 0;
-        // copy S in, merging groups that are contiguous in the host buffer
         int64_t run_src = -1, run_dst = 0, run_len = 0;
         for (int g = cut[c]; g < cut[c + 1]; ++g) {
             const int f = plan->f_slot[groups[g].prec_id];
@@ -714,8 +735,8 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
                     run_len += sb;
                 } else {
                     if (run_len > 0)
-                        BF_CK(plan, cudaMemcpyAsync(plan->x_s[i] + run_dst, (const uint8_t *)S_host + run_src, run_len,
-                                                    cudaMemcpyHostToDevice, st));
+                        BF_CK(plan, cudaMemcpyAsync(plan->x_s[k] + run_dst, (const uint8_t *)S_host + run_src, run_len,
+                                                    cudaMemcpyHostToDevice, plan->x_in));
                     run_src = groups[g].s_off;
                     run_dst = so;
                     run_len = sb;
@@ -725,12 +746,18 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
             ro += (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
         }
         if (run_len > 0)
-            BF_CK(plan, cudaMemcpyAsync(plan->x_s[i] + run_dst, (const uint8_t *)S_host + run_src, run_len,
-                                        cudaMemcpyHostToDevice, st));
-        if ((s = enqueue_apply(plan, plan->x_s[i], nullptr, local.data(), (int32_t)local.size(), prec, plan->x_r[i], st,
-                               0)) != BF_OK)
+            BF_CK(plan, cudaMemcpyAsync(plan->x_s[k] + run_dst, (const uint8_t *)S_host + run_src, run_len,
+                                        cudaMemcpyHostToDevice, plan->x_in));
+        BF_CK(plan, cudaEventRecord(plan->x_in_done[k], plan->x_in));
+        // the product, once S is in and the slot's previous R has left
+        BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_in_done[k], 0));
+        if (reuse) BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_out_done[k], 0));
+        if ((s = enqueue_apply(plan, plan->x_s[k], nullptr, local.data(), (int32_t)local.size(), prec, plan->x_r[k],
+                               plan->x_run, 0)) != BF_OK)
             return s;
+        BF_CK(plan, cudaEventRecord(plan->x_run_done[k], plan->x_run));
         // copy R out, merging contiguous destinations
+        BF_CK(plan, cudaStreamWaitEvent(plan->x_out, plan->x_run_done[k], 0));
         int64_t rsrc = 0, rdst = -1, rlen = 0;
         for (int g = cut[c]; g < cut[c + 1]; ++g) {
             const int64_t rb = (int64_t)groups[g].n_blocks * R_BLOCK_BYTES;
@@ -740,20 +767,22 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
                 rlen += rb;
             } else {
                 if (rlen > 0)
-                    BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[i] + rsrc, rlen,
-                                                cudaMemcpyDeviceToHost, st));
+                    BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[k] + rsrc, rlen,
+                                                cudaMemcpyDeviceToHost, plan->x_out));
                 rsrc = lo;
                 rdst = groups[g].r_off;
                 rlen = rb;
             }
         }
         if (rlen > 0)
-            BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[i] + rsrc, rlen, cudaMemcpyDeviceToHost, st));
+            BF_CK(plan, cudaMemcpyAsync((uint8_t *)R_host + rdst, plan->x_r[k] + rsrc, rlen, cudaMemcpyDeviceToHost,
+                                        plan->x_out));
+        BF_CK(plan, cudaEventRecord(plan->x_out_done[k], plan->x_out));
     }
-    BF_CK(plan, cudaEventRecord(plan->xfer_ev[0], plan->xfer[0]));
-    BF_CK(plan, cudaEventRecord(plan->xfer_ev[1], plan->xfer[1]));
-    BF_CK(plan, cudaStreamWaitEvent(user, plan->xfer_ev[0], 0));
-    BF_CK(plan, cudaStreamWaitEvent(user, plan->xfer_ev[1], 0));
+    // every copy-in feeds a kernel and every kernel a copy-out, so the last
+    // copy-out completes after all of this call's work
+    BF_CK(plan, cudaEventRecord(plan->x_end, plan->x_out));
+    BF_CK(plan, cudaStreamWaitEvent(user, plan->x_end, 0));
     return BF_OK;
 }
 

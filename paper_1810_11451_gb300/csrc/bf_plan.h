@@ -60,6 +60,17 @@ struct WorkBuf {
 
 }  // namespace bfi
 
+// Host-buffer pipeline: staging slots and the S + R bytes of one chunk.
+#ifndef BF_XFER_SLOTS
+#define BF_XFER_SLOTS 3
+#endif
+#ifndef BF_HOST_CHUNK_BYTES
+#define BF_HOST_CHUNK_BYTES (32 << 20)
+#endif
+#ifndef BF_HOST_CHUNK_FIRST
+#define BF_HOST_CHUNK_FIRST (2 << 20)
+#endif
+
 struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
     int simt_resident = 2;  // CTAs of the CUDA-core kernel that fit on one SM
@@ -71,7 +82,7 @@ struct bf_plan_s {
     float *w_scale = nullptr;
     int *d_status = nullptr;
     // work-list ring
-    bfi::WorkBuf ring[16];
+    bfi::WorkBuf ring[64];  // one per call in flight; also caches repeated lists
     int ring_next = 0;
     bfi::WorkList scratch_wl;
     // prep staging
@@ -82,13 +93,16 @@ struct bf_plan_s {
     double *en_d = nullptr;
     uint8_t *en_h = nullptr;
     size_t en_cap = 0, en_hcap = 0;
-    // graph capture and host-buffer pipeline
+    // graph capture
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t xfer[2] = {nullptr, nullptr};
-    cudaEvent_t xfer_ev[3] = {nullptr, nullptr, nullptr};
-    uint8_t *x_s[2] = {nullptr, nullptr}, *x_r[2] = {nullptr, nullptr};
-    size_t x_scap[2] = {0, 0}, x_rcap[2] = {0, 0};
-    int64_t host_chunk_bytes = 24 << 20;
+    // host-buffer pipeline: a copy-in, a compute and a copy-out stream over a
+    // ring of BF_XFER_SLOTS device staging slots (S and R of one chunk each)
+    cudaStream_t x_in = nullptr, x_run = nullptr, x_out = nullptr;
+    cudaEvent_t x_start = nullptr, x_end = nullptr;
+    cudaEvent_t x_in_done[BF_XFER_SLOTS] = {}, x_run_done[BF_XFER_SLOTS] = {}, x_out_done[BF_XFER_SLOTS] = {};
+    uint8_t *x_s[BF_XFER_SLOTS] = {}, *x_r[BF_XFER_SLOTS] = {};
+    size_t x_scap[BF_XFER_SLOTS] = {}, x_rcap[BF_XFER_SLOTS] = {};
+    int64_t host_chunk_bytes = BF_HOST_CHUNK_BYTES;
     // tuning and counters
     bfi::TuneTable tune;
     int64_t launches = 0;

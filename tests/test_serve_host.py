@@ -30,11 +30,18 @@ def test_jobs_complete_in_order_with_latency(bf):
     srv = bf.bf_serve_create(None, n_slots=1, max_batch_jobs=1, hbm_budget_bytes=1 << 30, fake_device_us=300)
     try:
         t0 = bf.bf_now_ns()
-        tickets = [bf.bf_submit(srv, job_groups(2), bf.BF_FP32, FAKE_S, FAKE_R, cell=i) for i in range(5)]
+        arrivals, tickets = [], []
+        for i in range(5):
+            a = bf.bf_now_ns()  # explicit arrival stamps: latency = completion - arrival exactly
+            arrivals.append(a)
+            tickets.append(bf.bf_submit(srv, job_groups(2), bf.BF_FP32, FAKE_S, FAKE_R, cell=i, arrival_ns=a))
         lats = [bf.bf_wait(srv, t, 5_000_000) for t in tickets]
         assert all(l >= 300 for l in lats)
-        assert lats == sorted(lats)  # one slot, FIFO: later jobs wait longer
-        assert lats[-1] >= 5 * 300
+        done_us = [a * 1e-3 + l for a, l in zip(arrivals, lats)]
+        # one slot, FIFO: each job completes at least one device time after the
+        # one before it, whatever the gaps between the submissions
+        assert all(d1 - d0 >= 0.99 * 300 for d0, d1 in zip(done_us, done_us[1:]))
+        assert done_us[-1] - t0 * 1e-3 >= 0.99 * 5 * 300
         st = bf.bf_serve_get_stats(srv)
         assert st["submitted"] == 5 and st["completed"] == 5 and st["launches"] == 5
         assert bf.bf_now_ns() - t0 >= 5 * 300_000
