@@ -345,65 +345,83 @@ extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const 
 }
 
 // ------------------------------------------------------------------ work lists
-// Tiles of 1 or 2 consecutive blocks of one group (the tile size per f bucket
-// comes from the autotune table); the run of tiles is split into n_cta
-// contiguous ranges of about equal cost (measured ns per block once tuned,
-// bytes moved before), so each CTA loads a precoder once per range and
-// streams its S blocks.
+// The blocks of the batch, in group order, are split into n_cta contiguous
+// ranges of about equal cost (measured ns per block once tuned, bytes moved
+// before), at block granularity: CTA loads differ by at most about one block.
+// Within a range, each group's run of blocks becomes tiles of up to
+// tile_blocks consecutive blocks (the size per f bucket comes from the
+// autotune table), so each CTA loads a precoder once per run and streams its
+// S blocks.
 void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *groups, int32_t n_groups,
                     bf_precision prec, bool held, int max_cta, int64_t r_block_stride, WorkList &wl) {
-    // count first, so the arrays are sized once (the buffers persist across
-    // calls in the plan, so steady-state scheduling allocates nothing)
-    int n_tiles = 0;
-    for (int g = 0; g < n_groups; ++g) {
-        const int tb = tune.tile_blocks_for(prec, f_slot[groups[g].prec_id]);
-        n_tiles += (groups[g].n_blocks + tb - 1) / tb;
-    }
-    wl.tiles.resize(n_tiles);
-    wl.cost.resize(n_tiles);
-    Tile *tiles = wl.tiles.data();
+    // per-group block cost, and the total (the buffers persist across calls in
+    // the plan, so steady-state scheduling allocates nothing)
+    wl.cost.resize(n_groups);
     double *cost = wl.cost.data();
     double total = 0;
-    int blk = 0, n = 0;
+    int64_t n_blocks = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        const int f = f_slot[groups[g].prec_id];
+        const int64_t sb = held ? held_block_bytes(f, prec == BF_BF16X3 ? 2 : 1) : (int64_t)f * S_BYTES_PER_F;
+        cost[g] = tune.cost(prec, f, 1, (double)(sb + R_BLOCK_BYTES));
+        total += cost[g] * groups[g].n_blocks;
+        n_blocks += groups[g].n_blocks;
+    }
+    wl.tiles.clear();
+    wl.cta_begin.clear();
+    if (n_blocks == 0) {  // nothing to launch: one empty range
+        wl.cta_begin.assign(2, 0);
+        return;
+    }
+    const int n_cta = (int)std::max<int64_t>(1, std::min<int64_t>(max_cta, n_blocks));
+    wl.tiles.reserve((size_t)n_blocks);
+    wl.cta_begin.reserve((size_t)n_cta + 1);
+    wl.cta_begin.push_back(0);
+    // midpoint rule: block k goes to CTA floor((cum + cost/2) / (total / n_cta)),
+    // clamped so that ranges stay contiguous and no CTA is left empty
+    const double per_cost = total > 0 ? n_cta / total : 0.0;
+    double cum = 0;
+    int cur = 0, blk = 0;
+    int64_t k = 0;
     for (int g = 0; g < n_groups; ++g) {
         const bf_group &gr = groups[g];
         const int f = f_slot[gr.prec_id];
         const int64_t sb = held ? held_block_bytes(f, prec == BF_BF16X3 ? 2 : 1) : (int64_t)f * S_BYTES_PER_F;
         const int tile_blocks = tune.tile_blocks_for(prec, f);
-        const double c1 = tune.cost(prec, f, 1, (double)(sb + R_BLOCK_BYTES));
-        for (int b0 = 0; b0 < gr.n_blocks; b0 += tile_blocks, ++n) {
-            Tile &t = tiles[n];
-            t.s_off = gr.s_off + (int64_t)b0 * sb;
-            t.r_off = gr.r_off + (int64_t)b0 * r_block_stride;
+        int open = -1;  // index of the tile being filled (this group, this CTA)
+        for (int b = 0; b < gr.n_blocks; ++b, ++k) {
+            int c = (int)((cum + 0.5 * cost[g]) * per_cost);
+            const int lo = (int)std::max<int64_t>(cur, n_cta - (n_blocks - k));
+            const int hi = std::min(k > 0 ? cur + 1 : 0, n_cta - 1);
+            c = std::min(std::max(c, lo), hi);
+            if (c != cur) {
+                cur = c;
+                wl.cta_begin.push_back((int32_t)wl.tiles.size());
+                open = -1;
+            }
+            cum += cost[g];
+            if (open >= 0 && wl.tiles[open].nblk < tile_blocks) {
+                ++wl.tiles[open].nblk;
+                continue;
+            }
+            Tile t;
+            t.s_off = gr.s_off + (int64_t)b * sb;
+            t.r_off = gr.r_off + (int64_t)b * r_block_stride;
             t.prec = gr.prec_id;
-            t.sblk = blk + b0;
+            t.sblk = blk + b;
             t.f = (int16_t)f;
-            t.nblk = (int16_t)std::min(tile_blocks, gr.n_blocks - b0);
+            t.nblk = 1;
             t.flags = 0;
-            cost[n] = c1 * t.nblk;
-            total += cost[n];
+            open = (int)wl.tiles.size();
+            wl.tiles.push_back(t);
         }
         blk += gr.n_blocks;
     }
-    const int n_cta = std::max(1, std::min(max_cta, n_tiles));
-    wl.cta_begin.assign(n_cta + 1, n_tiles);
-    wl.cta_begin[0] = 0;
-    // midpoint rule: tile t goes to CTA floor((cum + cost/2) / (total / n_cta)),
-    // clamped so that ranges stay contiguous and no CTA is left empty
-    double cum = 0;
-    int cur = 0;
-    const double per_cost = total > 0 ? n_cta / total : 0.0;
-    for (int t = 0; t < n_tiles; ++t) {
-        int c = (int)((cum + 0.5 * cost[t]) * per_cost);
-        const int lo = std::max(cur, n_cta - (n_tiles - t));
-        const int hi = std::min(t > 0 ? cur + 1 : 0, n_cta - 1);
-        c = std::min(std::max(c, lo), hi);
-        while (cur < c) wl.cta_begin[++cur] = t;
-        cum += cost[t];
-    }
-    while (cur < n_cta) wl.cta_begin[++cur] = n_tiles;
+    const int n_tiles = (int)wl.tiles.size();
+    wl.cta_begin.push_back(n_tiles);
+    Tile *tiles = wl.tiles.data();
     // precoder-run flags within each CTA's range (tiles with f > 0 only)
-    for (int c = 0; c < n_cta; ++c) {
+    for (int c = 0; c + 1 < (int)wl.cta_begin.size(); ++c) {
         int prev = -1;
         int last_idx = -1;
         for (int t = wl.cta_begin[c]; t < wl.cta_begin[c + 1]; ++t) {

@@ -120,11 +120,11 @@ def test_scheduler_covers_every_block_once(bf, max_cta):
     # contiguous CTA ranges covering all tiles, none empty
     assert begin[0] == 0 and begin[-1] == len(tiles)
     assert all(begin[c] < begin[c + 1] for c in range(len(begin) - 1))
-    assert len(begin) - 1 == min(max_cta, len(tiles))
-    # cost balance: no CTA above the mean by more than one tile's cost
+    assert len(begin) - 1 == min(max_cta, batch.total_blocks)
+    # cost balance at block granularity: no CTA above the mean by more than one block's cost
     cost = np.array([t.n_blocks * (480 * t.f + 30720) for t in tiles], float)
     per = [cost[begin[c]:begin[c + 1]].sum() for c in range(len(begin) - 1)]
-    assert max(per) <= cost.sum() / len(per) + 2 * cost.max()
+    assert max(per) <= cost.sum() / len(per) + (480 * 36 + 30720)
     # precoder-run flags
     for c in range(len(begin) - 1):
         run = [t for t in tiles[begin[c]:begin[c + 1]] if t.f > 0]
@@ -144,11 +144,16 @@ def test_scheduler_rejects_bad_input(bf):
     assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
     ga, n = bf.make_groups([(0, 2, 0, 0)])
     assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 1, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
-    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == 1
+    # two blocks over up to four CTAs: one block (one tile) each; on one CTA, one two-block tile
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == 2
+    assert ncta.value == 2
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 1, None, 0, None, ctypes.byref(ncta)) == 1
 
 
 def test_scheduler_empty_and_zero_f(bf):
-    tiles, begin = schedule(bf, [0, 3], [(0, 3, 0, 0), (1, 0, 0, 0)], bf.BF_FP32, 0, 4)
+    tiles, begin = schedule(bf, [0, 3], [(0, 3, 0, 0), (1, 0, 0, 0)], bf.BF_FP32, 0, 1)
     assert [t.n_blocks for t in tiles] == [2, 1] and all(t.flags == 0 for t in tiles)
+    tiles, begin = schedule(bf, [0, 3], [(0, 3, 0, 0), (1, 0, 0, 0)], bf.BF_FP32, 0, 4)
+    assert [t.n_blocks for t in tiles] == [1, 1, 1] and begin == [0, 1, 2, 3]
     tiles, begin = schedule(bf, [3], [], bf.BF_FP32, 0, 4)
     assert tiles == [] and begin == [0, 0]
