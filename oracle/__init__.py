@@ -17,6 +17,10 @@ Contents
     lo = bf16(x - hi), all decided in FP32 as the GPU does).
   * `apply_terms`: the FP64 product of already-encoded operands, used to check
     the tensor-core kernels' mechanics tightly.
+  * `circular_filter`, `dft`: the fast-convolution filter y = IFFT(MULT(FFT(s)))
+    of Sec. III (filter equation, Fig. 4), N = 2048, evaluated by its
+    definition as a circular convolution, and the DFT by its definition, both
+    in `bf_filter_oracle.c` (FP64).
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bf_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "bf_filter_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "libbf_oracle.so")
 _lib = None
 
@@ -38,11 +43,12 @@ def build(out_path: str = _LIB_PATH, mutant: int = 0, force: bool = False) -> st
 
     `mutant` > 0 plants one of the deliberate mistakes listed in the C source
     (used only by the tests that show the pins catch mistakes)."""
-    if not force and os.path.exists(out_path) and os.path.getmtime(out_path) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(out_path) and \
+            os.path.getmtime(out_path) >= max(os.path.getmtime(f) for f in _SRCS):
         return out_path
     tmp = out_path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           f"-DBFO_MUTANT={int(mutant)}", _SRC, "-o", tmp]
+           f"-DBFO_MUTANT={int(mutant)}"] + _SRCS + ["-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out_path)
     return out_path
@@ -53,6 +59,11 @@ def _bind(path: str):
     lib.bfo_apply_blocks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.bfo_apply_blocks.restype = None
+    lib.bfo_circular_filter.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+    lib.bfo_circular_filter.restype = None
+    lib.bfo_dft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
+    lib.bfo_dft.restype = None
     lib.bfo_num_threads.restype = ctypes.c_int
     lib.bfo_mutant_id.restype = ctypes.c_int
     return lib
@@ -220,3 +231,44 @@ def apply_terms(W_terms, S_terms, pairs, scale: float = 1.0, _lib=None) -> np.nd
         t = apply_blocks(W_terms[a], S_terms[b_], _lib)
         R = t if R is None else R + t
     return R * scale
+
+
+# --------------------------------------------------------------------------
+# The fast-convolution filter (Sec. III, filter equation and Fig. 4)
+# --------------------------------------------------------------------------
+def _c128(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+
+def circular_filter(h: np.ndarray, s: np.ndarray, _lib=None) -> np.ndarray:
+    """y = IFFT(FFT(h) * FFT(s)) for every signal, evaluated as the circular
+    convolution y[n] = sum_m h[m] s[(n - m) mod N] in FP64.
+
+    h: (N,) or (n_taps <= N,) complex filter sequence (zero-padded to N);
+    s: (n_sig, N) complex signals. Returns (n_sig, N) complex128."""
+    s = _c128(s)
+    if s.ndim == 1:
+        s = s[None, :]
+    n = s.shape[-1]
+    hp = np.zeros(n, np.complex128)
+    h = np.asarray(h, dtype=np.complex128).ravel()
+    assert h.size <= n
+    hp[:h.size] = h
+    y = np.empty_like(s)
+    L = _lib or lib()
+    L.bfo_circular_filter(int(n), int(s.shape[0]), hp.ctypes.data, s.ctypes.data, y.ctypes.data)
+    return y
+
+
+def dft(x: np.ndarray, inverse: bool = False, _lib=None) -> np.ndarray:
+    """The DFT by its definition along the last axis: X[k] = sum_j x[j]
+    e^{-2 pi i j k / N} (inverse=True: the e^{+...} sum divided by N)."""
+    x = _c128(x)
+    shp = x.shape
+    x2 = x.reshape(-1, shp[-1])
+    X = np.empty_like(x2)
+    L = _lib or lib()
+    L.bfo_dft(int(shp[-1]), 1 if inverse else -1, int(x2.shape[0]), x2.ctypes.data, X.ctypes.data)
+    if inverse:
+        X /= shp[-1]
+    return X.reshape(shp)

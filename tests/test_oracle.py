@@ -210,6 +210,122 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
     assert failed, f"mutant {mutant} passed every pin"
 
 
+# ---------------------------------------------------------------- filter pins
+# The filter y = IFFT(MULT(FFT(s))) (Sec. III, filter equation, Fig. 4) with
+# the unnormalised forward DFT and 1/N in the inverse is the circular
+# convolution of the filter sequence h with s. The pins below fix the oracle
+# by facts that do not come from it: a hand-worked N = 4 case, the identity
+# and shifted-impulse closed forms, the convolution theorem through numpy's
+# FFT, linearity, and the DFT's closed forms (impulse, constant, pure tone),
+# Parseval's identity and numpy's FFT for the definition-based DFT.
+def pin_filter_hand_example(L):
+    """N = 4, h = [1, i, 0, 0], s = [1, 0, 0, 1]: y[0] = h0 s0 + h1 s3 = 1 + i,
+    y[1] = h1 s0 = i, y[2] = 0, y[3] = h0 s3 = 1 (worked by hand)."""
+    y = oracle.circular_filter(np.array([1, 1j, 0, 0]), np.array([[1, 0, 0, 1]]), L)[0]
+    return np.array_equal(y, np.array([1 + 1j, 1j, 0, 1]))
+
+
+def pin_filter_identity(L):
+    """h = delta: y = s exactly."""
+    rng = np.random.default_rng(40)
+    s = _rand_c(rng, (3, 64))
+    h = np.zeros(64, complex)
+    h[0] = 1
+    return np.array_equal(oracle.circular_filter(h, s, L), s)
+
+
+def pin_filter_shifted_impulse(L):
+    """s = delta[n - n0]: y[n] = h[(n - n0) mod N] exactly (the wrap included)."""
+    rng = np.random.default_rng(41)
+    n = 128
+    h = _rand_c(rng, 100)
+    hp = np.zeros(n, complex)
+    hp[:100] = h
+    for n0 in (0, 1, 37, 127):
+        s = np.zeros((1, n), complex)
+        s[0, n0] = 1
+        if not np.array_equal(oracle.circular_filter(h, s, L)[0], np.roll(hp, n0)):
+            return False
+    return True
+
+
+def pin_filter_convolution_theorem(L):
+    """y = ifft(fft(h) * fft(s)) through numpy's FFT, at N = 2048, to 1e-12."""
+    rng = np.random.default_rng(42)
+    b = wl.config_filter_small(n_sig=4)
+    hp = np.zeros(b.n, complex)
+    hp[:b.h.size] = b.h
+    ref = np.fft.ifft(np.fft.fft(hp)[None, :] * np.fft.fft(b.s, axis=1), axis=1)
+    y = oracle.circular_filter(b.h, b.s, L)
+    return np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def pin_filter_linearity(L):
+    rng = np.random.default_rng(43)
+    h = _rand_c(rng, 50)
+    s1, s2 = _rand_c(rng, (2, 256)), _rand_c(rng, (2, 256))
+    a, c = 0.75 - 0.5j, -1.25 + 2j
+    lhs = oracle.circular_filter(h, a * s1 + c * s2, L)
+    rhs = a * oracle.circular_filter(h, s1, L) + c * oracle.circular_filter(h, s2, L)
+    return np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+
+
+def pin_dft_closed_forms(L):
+    """DFT(delta) = 1, DFT(1) = N delta, DFT(e^{2 pi i k0 n / N}) = N delta[k - k0]."""
+    n = 64
+    d = np.zeros(n, complex)
+    d[0] = 1
+    if np.max(np.abs(oracle.dft(d, _lib=L) - 1)) > 1e-13:
+        return False
+    e = np.zeros(n, complex)
+    e[0] = n
+    if np.max(np.abs(oracle.dft(np.ones(n, complex), _lib=L) - e)) > 1e-11:
+        return False
+    k0 = 5
+    tone = np.exp(2j * np.pi * k0 * np.arange(n) / n)
+    e = np.zeros(n, complex)
+    e[k0] = n
+    return np.max(np.abs(oracle.dft(tone, _lib=L) - e)) <= 1e-10
+
+
+def pin_dft_parseval_and_library(L):
+    rng = np.random.default_rng(44)
+    x = _rand_c(rng, (2, 2048))
+    X = oracle.dft(x, _lib=L)
+    if abs(np.sum(np.abs(X) ** 2) - 2048 * np.sum(np.abs(x) ** 2)) > 1e-10 * np.sum(np.abs(X) ** 2):
+        return False
+    if np.max(np.abs(X - np.fft.fft(x, axis=1))) > 1e-10 * np.max(np.abs(X)):
+        return False
+    return np.max(np.abs(oracle.dft(X, inverse=True, _lib=L) - x)) <= 1e-12 * np.max(np.abs(x))
+
+
+FILTER_PINS = [pin_filter_hand_example, pin_filter_identity, pin_filter_shifted_impulse,
+               pin_filter_convolution_theorem, pin_filter_linearity, pin_dft_closed_forms,
+               pin_dft_parseval_and_library]
+
+
+@pytest.mark.parametrize("pin", FILTER_PINS, ids=[p.__name__ for p in FILTER_PINS])
+def test_filter_oracle_pin(pin, oracle_lib):
+    assert pin(oracle_lib)
+
+
+def test_filter_dimensions_fixture():
+    with open(os.path.join(GOLDEN, "filter_dimensions.txt")) as fh:
+        vals = dict(line.split() for line in fh if line.strip() and not line.startswith("#"))
+    assert int(vals["n"]) == wl.FILTER_N
+
+
+# Filter mistakes (BFO_MUTANT 8..10 in bf_filter_oracle.c): correlation instead
+# of convolution, no circular wrap, conjugated taps.
+@pytest.mark.parametrize("mutant", [8, 9, 10])
+def test_planted_filter_mistakes_are_caught(mutant, tmp_path):
+    path = oracle.build(str(tmp_path / f"libbf_oracle_m{mutant}.so"), mutant=mutant, force=True)
+    L = oracle.load_variant(path)
+    assert L.bfo_mutant_id() == mutant
+    failed = [p.__name__ for p in FILTER_PINS if not p(L)]
+    assert failed, f"mutant {mutant} passed every filter pin"
+
+
 # ---------------------------------------------------------------- accuracy report
 def test_errnorm_closed_form():
     rng = np.random.default_rng(20)

@@ -9,6 +9,9 @@ row per antenna (64 antennas, Sec. II: 4 x 8 x 2 transceivers), S is f x b with
 one row per parallel flow and one column per resource element, b = 60, and
 0 <= f <= 36. W is constant while S changes, so many S blocks share one W.
 
+The filter workload (Sec. III, filter equation and Fig. 4) is drawn here too:
+blocks of N = 2048 complex time-domain samples and one filter sequence.
+
 Layouts (the readings used throughout the library):
   * complex numbers are interleaved (re, im) pairs;
   * W is row-major n_ant x f (antenna-major), S is row-major f x b (flow-major),
@@ -33,7 +36,11 @@ __all__ = [
     "integer_precoder", "complex_noise", "geometric_group_sizes",
     "config_small", "config_fullband", "config_uneven", "config_reduced",
     "config_exact_integer", "serving_schedule", "ServingJob",
+    "FILTER_N", "FilterBatch", "filter_taps", "filter_signals",
+    "config_filter_small", "config_filter_tti", "config_filter_bench",
 ]
+
+FILTER_N = 2048  # FFT size of the filter (Sec. III: all sizes are 2048)
 
 
 def qam_levels(order: int) -> np.ndarray:
@@ -284,3 +291,72 @@ def serving_schedule(seed: int = 5, n_cells: int = 8, n_tti: int = 20000, tti_s:
                                    int(f_epoch[c, e]), e))
     jobs.sort(key=lambda j: (j.arrival_s, j.cell))
     return jobs
+
+
+# --------------------------------------------------------------------------
+# Fast-convolution filter inputs (Sec. III, filter equation and Fig. 4)
+# --------------------------------------------------------------------------
+@dataclass
+class FilterBatch:
+    """n_sig signal blocks of n complex samples (row-major, signal-major) and
+    one filter sequence h of n_taps <= n taps (zero-padded to n by the filter)."""
+    h: np.ndarray
+    s: np.ndarray
+    name: str = ""
+    seed: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.s.shape[1])
+
+    @property
+    def n_sig(self) -> int:
+        return int(self.s.shape[0])
+
+    def algorithmic_bytes(self, elem_bytes: int = 8) -> int:
+        """Each signal read once and each output written once (the 2048-point
+        spectrum of the filter is read from cache, not counted)."""
+        return int(2 * self.n_sig * self.n * elem_bytes)
+
+    def flops(self) -> int:
+        """Conventional count: 5 N log2 N real flops per complex FFT, two FFTs
+        and one complex multiply (6 flops) per sample per signal."""
+        n = self.n
+        return int(self.n_sig * (2 * 5 * n * int(np.log2(n)) + 6 * n))
+
+    def rounded(self, dtype=np.complex64) -> "FilterBatch":
+        return FilterBatch(self.h.astype(dtype).astype(np.complex128), self.s.astype(dtype).astype(np.complex128),
+                           self.name, self.seed)
+
+
+def filter_taps(rng: np.random.Generator, n_taps: int, decay: float = 64.0) -> np.ndarray:
+    """Channel-like FIR: h[m] ~ CN(0, e^{-m/decay}), normalised to unit energy."""
+    m = np.arange(n_taps)
+    h = complex_noise(rng, 1.0, (n_taps,)) * np.sqrt(np.exp(-m / decay))
+    return h / np.sqrt(np.sum(np.abs(h) ** 2))
+
+
+def filter_signals(rng: np.random.Generator, n_sig: int, n: int = FILTER_N) -> np.ndarray:
+    """Time-domain samples CN(0, 1) (the sample statistics of an OFDM signal)."""
+    return complex_noise(rng, 1.0, (n_sig, n))
+
+
+def config_filter_small(seed: int = 10, n_sig: int = 64, n_taps: int = 256) -> FilterBatch:
+    """64 blocks of 2048 samples, a 256-tap filter."""
+    rng = np.random.default_rng(seed)
+    return FilterBatch(filter_taps(rng, n_taps), filter_signals(rng, n_sig), f"filter_x{n_sig}", seed)
+
+
+def config_filter_tti(seed: int = 11, n_ant: int = N_ANT, n_sym: int = 14, n_taps: int = 256) -> FilterBatch:
+    """One slot: one 2048-sample block per antenna and OFDM symbol, 64 x 14 = 896."""
+    rng = np.random.default_rng(seed)
+    return FilterBatch(filter_taps(rng, n_taps), filter_signals(rng, n_ant * n_sym),
+                       f"filter_tti_{n_ant}x{n_sym}", seed)
+
+
+def config_filter_bench(seed: int = 12, n_ant: int = N_ANT, n_sym: int = 14, n_slots: int = 16,
+                        n_taps: int = 256) -> FilterBatch:
+    """16 slots of 64 antennas x 14 symbols: 14,336 blocks, 235 MB in and out."""
+    rng = np.random.default_rng(seed)
+    return FilterBatch(filter_taps(rng, n_taps), filter_signals(rng, n_ant * n_sym * n_slots),
+                       f"filter_{n_slots}slots", seed)
