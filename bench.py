@@ -408,6 +408,75 @@ def fused_output_leg(torch, bf, plan, batch, ref, stream, steps=2000, n_sets=4):
     return out
 
 
+FILTER_SAMPLE = 16  # blocks of the filter workload checked against the oracle
+
+
+def filter_cpu_leg(b):
+    """Part of the CPU-baseline leg: the oracle's y for FILTER_SAMPLE blocks
+    spread over the filter batch, and its rate on those blocks."""
+    import oracle
+    idx = np.unique(np.linspace(0, b.n_sig - 1, FILTER_SAMPLE).astype(int))
+    rb = b.rounded()
+    t0 = time.perf_counter()
+    ref = oracle.circular_filter(rb.h, rb.s[idx])
+    dt = time.perf_counter() - t0
+    return idx, ref, {"us_per_block": dt / len(idx) * 1e6, "cores": oracle.num_threads(), "kind": "oracle",
+                      "sample": f"{len(idx)} of {b.n_sig} blocks, direct FP64 circular convolution"}
+
+
+def filter_leg(torch, bf, b, sample, stream, steps=100):
+    """Fast-convolution filter y = IFFT(MULT(FFT(s))) (Sec. III, Fig. 4, N = 2048)
+    over 16 slots x 64 antennas x 14 symbols = 14,336 blocks: 235 MB read and
+    235 MB written per launch (inputs larger than L2), one fused kernel."""
+    from bfrun import to_device_c64
+    f = bf.bf_filter_create(2048)
+    h = to_device_c64(b.h, torch)
+    bf.bf_filter_set_taps(f, h, len(b.h), stream)
+    S = to_device_c64(b.s, torch)
+    Y = torch.empty_like(S)
+    for _ in range(5):
+        bf.bf_filter_apply(f, S, b.n_sig, Y, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = bf.bf_filter_launch_count(f)
+    e0.record(stream)
+    for _ in range(steps):
+        bf.bf_filter_apply(f, S, b.n_sig, Y, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = bf.bf_filter_launch_count(f) - n0
+    ms = e0.elapsed_time(e1) / steps
+    moved = b.algorithmic_bytes()
+    out = {"blocks": b.n_sig, "n": b.n, "kernel_ms": ms, "blocks_per_s": b.n_sig / ms * 1e3,
+           "us_per_block_amortised": ms * 1e3 / b.n_sig, "gflops_conventional": b.flops() / ms / 1e6,
+           "moved_bytes": moved, "moved_gbs": moved / ms / 1e6, "gpu_launches": int(launches),
+           "paper_context_us_per_filter": {"original": 27, "intel_fft_library": 19,
+                                           "hardware": "Intel Haswell (E9000 blade), one filter"}}
+    if sample is not None:
+        idx, ref, cpu = sample
+        y = Y.cpu().numpy().view(np.complex64).reshape(b.n_sig, b.n)[idx].astype(np.complex128)
+        out["rel_err"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+        out["cpu_baseline"] = cpu
+    # end to end: pinned host blocks in, filtered blocks out, every call
+    S_h = S.cpu().pin_memory()
+    Y_h = torch.empty_like(S_h).pin_memory()
+    for _ in range(2):
+        bf.bf_filter_apply_host(f, S_h, b.n_sig, Y_h, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        bf.bf_filter_apply_host(f, S_h, b.n_sig, Y_h, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / 5
+    out["e2e"] = {"ms": e2e_ms, "blocks_per_s": b.n_sig / e2e_ms * 1e3, "h2d_bytes": moved // 2,
+                  "d2h_bytes": moved // 2}
+    bf.bf_filter_destroy(f)
+    del S, Y, S_h, Y_h
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_leg(torch, bf, ttis, prec):
     """Continuous-batching serving of 8 cells in real time (0.5 ms TTIs)."""
     import workloads as wl
@@ -493,9 +562,13 @@ def main():
     extra = not args.no_extra and rank == 0
     b_uneven = wl.config_uneven() if extra else None
     b_reduced = wl.config_reduced() if extra else None
+    b_filter = wl.config_filter_bench() if extra else None
+    filter_sample = None
     if rank == 0 and not args.no_cpu:
         cpu, ref = cpu_baseline(batch)
         refs = cpu_references({"fullband": ref}, {"uneven": b_uneven, "reduced": b_reduced})
+        if b_filter is not None:
+            filter_sample = filter_cpu_leg(b_filter)
         ref_full = refs.pop("fullband")
         Rref_d = to_device_ref(torch, ref_full)
         acc = {}
@@ -522,6 +595,7 @@ def main():
         legs["reduced"] = reduced_leg(torch, bf, plan, b_reduced, ref_d, stream)
         del ref_d
         torch.cuda.empty_cache()
+        legs["filter"] = filter_leg(torch, bf, b_filter, filter_sample, stream)
         legs["serving_bf16x3"] = serving_leg(torch, bf, args.serving_ttis, bf.BF_BF16X3)
         legs["serving_fp32"] = serving_leg(torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
     status = bf.bf_device_status(plan)

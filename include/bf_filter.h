@@ -1,0 +1,80 @@
+/*
+ * bf_filter.h -- C ABI of the fast-convolution filter of libbf (GB300, sm_103a).
+ *
+ * The operation (Sec. III, the filter equation and Fig. 4): for each block s
+ * of N = 2048 complex samples,
+ *     y = IFFT( MULT( FFT(s) ) ),
+ * where MULT is the pointwise product with the FFT of the filter sequence h
+ * and all transforms have size 2048. Readings: FFT is the unnormalised DFT
+ * X[k] = sum_n x[n] e^{-2 pi i n k / N}; IFFT carries the 1/N. The result is
+ * then the circular convolution y[n] = sum_m h[m] s[(n - m) mod N].
+ *
+ * Conventions as in bf.h: complex values are interleaved FP32 pairs
+ * ("complex64"); "_dev" pointers are device memory owned by the caller;
+ * every call returns a bf_status, never aborts, and is asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) unless stated.
+ * A filter object is not thread-safe (one host thread at a time).
+ *
+ * Arithmetic: FP32 throughout (FP32 twiddles rounded from FP64 values, FP32
+ * butterflies), one fused kernel per call: each block is read once, both
+ * transforms and the product run on chip, and y is written once.
+ */
+#ifndef BF_FILTER_H
+#define BF_FILTER_H
+
+#include <stdint.h>
+
+#include "bf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_filter_s *bf_filter;
+
+/* Create a filter on the current CUDA device for transforms of n points.
+ * n must be 2048 (Sec. III); BF_EINVAL otherwise (checked before any CUDA
+ * call), BF_ECUDA without a usable device. The filter owns its twiddle table
+ * and the filter spectrum. No filter sequence is set yet. */
+bf_status bf_filter_create(int n, bf_filter *out);
+
+/* Free the filter (synchronises the device first). NULL is accepted. */
+bf_status bf_filter_destroy(bf_filter filter);
+
+/* Text of the filter's last error ("" if none); NULL gives the last error of
+ * a failed bf_filter_create. */
+const char *bf_filter_last_error(bf_filter filter);
+
+/* Set the filter sequence: h_dev holds n_taps complex64 taps (8-byte
+ * aligned), 1 <= n_taps <= n, zero-padded to n. The spectrum H = FFT(h) is
+ * computed on the device with the library's own forward transform, ordered on
+ * `stream`; later calls on other streams must be ordered after it. h_dev may
+ * be freed once `stream` has passed this call. */
+bf_status bf_filter_set_taps(bf_filter filter, const void *h_dev, int n_taps, void *stream);
+
+/* Copy the current spectrum H = FFT(h), n complex64 values, to H_dev (8-byte
+ * aligned). BF_ENOTFOUND if no filter sequence was set. */
+bf_status bf_filter_spectrum(bf_filter filter, void *H_dev, void *stream);
+
+/* y = IFFT(H * FFT(s)) for n_sig blocks: s_dev and y_dev hold n_sig x n
+ * complex64 values, block-major (block q at q*n*8 bytes), 16-byte aligned.
+ * y_dev may equal s_dev (each block is read completely before it is
+ * written); other overlaps are not allowed. n_sig = 0 is a no-op.
+ * BF_ENOTFOUND if no filter sequence was set. */
+bf_status bf_filter_apply(bf_filter filter, const void *s_dev, int64_t n_sig, void *y_dev, void *stream);
+
+/* The same with s and y in HOST memory (best pinned): blocks are copied in,
+ * filtered and copied out in chunks over internal copy-in, compute and
+ * copy-out streams. Ordered after `stream`; `stream` is ordered after its
+ * completion (synchronise `stream` before reading y_host). */
+bf_status bf_filter_apply_host(bf_filter filter, const void *s_host, int64_t n_sig, void *y_host,
+                               void *stream);
+
+/* Number of kernel launches issued by this filter so far. */
+int64_t bf_filter_launch_count(bf_filter filter);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_FILTER_H */

@@ -274,6 +274,70 @@ def bf_errnorm(plan, R_dev, Rref_dev, n_blocks: int, per_block_dev=None, stream=
     return float(tot[0]), float(tot[1])
 
 
+# ---------------------------------------------------------------- the filter (bf_filter.h)
+FILTER_N = 2048
+
+
+def _filter_sigs(L):
+    if not getattr(L, "_filter_sigs", False):
+        sig = {
+            "bf_filter_create": (c_int, [c_int, POINTER(c_void_p)]),
+            "bf_filter_destroy": (c_int, [c_void_p]),
+            "bf_filter_last_error": (c_char_p, [c_void_p]),
+            "bf_filter_set_taps": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+            "bf_filter_spectrum": (c_int, [c_void_p, c_void_p, c_void_p]),
+            "bf_filter_apply": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+            "bf_filter_apply_host": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+            "bf_filter_launch_count": (c_int64, [c_void_p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        L._filter_sigs = True
+    return L
+
+
+def bf_filter_last_error(filt=None) -> str:
+    return (_filter_sigs(lib()).bf_filter_last_error(filt) or b"").decode()
+
+
+def _fcheck(status: int, filt=None):
+    if status != BF_OK:
+        raise BfError(status, bf_filter_last_error(filt))
+
+
+def bf_filter_create(n: int = FILTER_N) -> int:
+    h = c_void_p()
+    _fcheck(_filter_sigs(lib()).bf_filter_create(int(n), ctypes.byref(h)))
+    return h.value
+
+
+def bf_filter_destroy(filt) -> None:
+    _filter_sigs(lib()).bf_filter_destroy(filt)
+
+
+def bf_filter_set_taps(filt, h_dev, n_taps: int, stream=None) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_set_taps(filt, _ptr(h_dev), int(n_taps), _stream(stream)), filt)
+
+
+def bf_filter_spectrum(filt, H_dev, stream=None) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_spectrum(filt, _ptr(H_dev), _stream(stream)), filt)
+
+
+def bf_filter_apply(filt, s_dev, n_sig: int, y_dev, stream=None) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_apply(filt, _ptr(s_dev), int(n_sig), _ptr(y_dev), _stream(stream)), filt)
+
+
+def bf_filter_apply_host(filt, s_host, n_sig: int, y_host, stream=None) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_apply_host(filt, _ptr(s_host), int(n_sig), _ptr(y_host), _stream(stream)),
+            filt)
+
+
+def bf_filter_launch_count(filt) -> int:
+    return int(_filter_sigs(lib()).bf_filter_launch_count(filt))
+
+
 def bf_plan_launch_count(plan) -> int:
     return int(lib().bf_plan_launch_count(plan))
 

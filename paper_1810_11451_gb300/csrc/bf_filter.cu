@@ -1,0 +1,455 @@
+// bf_filter.cu -- the fast-convolution filter y = IFFT(MULT(FFT(s))) of
+// Sec. III (filter equation, Fig. 4), N = 2048, FP32, one fused kernel.
+//
+// A team of 128 threads filters one block of 2048 samples; each thread holds
+// 16 complex values in registers. Both transforms are Stockham passes of
+// radix 16, 16 and 8 (2048 = 16 * 16 * 8): a pass reads the R values
+// x[j + m N/R] of butterfly j, multiplies them by e^{-+2 pi i m k / (Ns R)},
+// k = j mod Ns, takes their R-point DFT and writes them to
+// (j div Ns) Ns R + k + q Ns (Ns = 1, 16, 256). The first pass reads the
+// block straight from global memory; between passes the values go through a
+// padded shared-memory buffer (one pad word per 16 values keeps every access
+// free of bank conflicts); the last forward pass leaves in thread t exactly
+// the values X[t + 128 m], which is also what the first inverse pass needs,
+// so the spectrum product happens in registers and the inverse starts there.
+// The last inverse pass writes y in natural order, coalesced.
+//
+// The 1/N of the inverse is folded into the spectrum (a power of two, exact).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bf_filter.h"
+
+namespace bff {
+
+constexpr int N = 2048;
+constexpr int TEAM = 128;                 // threads per block of samples
+// Teams per CTA and CTAs per SM (compile-time knobs): 2 x 2 keeps the
+// transform's 16 values per thread and its temporaries in registers.
+#ifndef BF_FILTER_TEAMS
+#define BF_FILTER_TEAMS 2
+#endif
+#ifndef BF_FILTER_CTAS
+#define BF_FILTER_CTAS 2
+#endif
+constexpr int TEAMS = BF_FILTER_TEAMS;
+constexpr int THREADS = TEAM * TEAMS;
+constexpr int CTAS_PER_SM = BF_FILTER_CTAS;
+constexpr int EBUF = N + N / 16;          // padded exchange buffer (complex values)
+constexpr int SMEM_BYTES = (2 * N + TEAMS * EBUF) * 8;
+
+__host__ __device__ constexpr int pad(int e) { return e + (e >> 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a times e^{DIR i theta} given w = e^{-i theta}: forward (DIR = -1) uses w,
+// inverse (DIR = +1) its conjugate.
+template <int DIR>
+__device__ __forceinline__ float2 ctw(float2 a, float2 w) {
+    if (DIR < 0) return cmul(a, w);
+    return make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+// a times DIR * i
+template <int DIR>
+__device__ __forceinline__ float2 cmul_i(float2 a) {
+    return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// 4-point DFT in place, X_q = sum_m x_m e^{DIR 2 pi i m q / 4}.
+template <int DIR>
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = cmul_i<DIR>(csub(b, d));
+    a = cadd(s0, s1);
+    c = csub(s0, s1);
+    b = cadd(d0, d1);
+    d = csub(d0, d1);
+}
+
+// cos and sin of 2 pi k / 16 for k = 1, 2, 3 (pi/8, pi/4, 3 pi/8)
+constexpr float C8 = 0.923879532511286756f, S8 = 0.382683432365089772f, R2 = 0.707106781186547524f;
+
+// e^{DIR 2 pi i k / 16} for the k = m2 * q1 products of a 4 x 4 split
+template <int DIR>
+__device__ __forceinline__ float2 w16(int k) {
+    const float s = DIR < 0 ? -1.f : 1.f;
+    switch (k) {
+        case 1: return make_float2(C8, s * S8);
+        case 2: return make_float2(R2, s * R2);
+        case 3: return make_float2(S8, s * C8);
+        case 4: return make_float2(0.f, s);
+        case 6: return make_float2(-R2, s * R2);
+        case 9: return make_float2(-C8, -s * S8);
+        default: return make_float2(1.f, 0.f);
+    }
+}
+
+// 16-point DFT: m = 4 m1 + m2, q = q1 + 4 q2; 4-point DFTs over m1, the
+// twiddle e^{DIR 2 pi i m2 q1 / 16}, then 4-point DFTs over m2.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2) dft4<DIR>(v[m2], v[m2 + 4], v[m2 + 8], v[m2 + 12]);
+    // now v[m2 + 4 q1] = U[m2][q1]
+#pragma unroll
+    for (int m2 = 1; m2 < 4; ++m2)
+#pragma unroll
+        for (int q1 = 1; q1 < 4; ++q1) v[m2 + 4 * q1] = cmul(v[m2 + 4 * q1], w16<DIR>(m2 * q1));
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) dft4<DIR>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+    // v[4 q1 + q2] = V[q1 + 4 q2]: transpose the 4 x 4 index grid
+    float2 o[16];
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) o[q1 + 4 * q2] = v[4 * q1 + q2];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = o[q];
+}
+
+// 8-point DFT: m = 2 m1 + m2, q = q1 + 4 q2; 4-point DFTs over m1, the
+// twiddle e^{DIR 2 pi i m2 q1 / 8}, then 2-point DFTs over m2.
+template <int DIR>
+__device__ __forceinline__ void dft8(float2 (&u)[8]) {
+    dft4<DIR>(u[0], u[2], u[4], u[6]);
+    dft4<DIR>(u[1], u[3], u[5], u[7]);
+    // u[m2 + 2 q1] = U[m2][q1]
+    u[3] = cmul(u[3], w16<DIR>(2));   // e^{DIR 2 pi i / 8}
+    u[5] = cmul_i<DIR>(u[5]);         // e^{DIR 2 pi i 2 / 8}
+    u[7] = cmul(u[7], w16<DIR>(6));   // e^{DIR 2 pi i 3 / 8}
+    float2 o[8];
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) {
+        o[q1] = cadd(u[2 * q1], u[2 * q1 + 1]);
+        o[q1 + 4] = csub(u[2 * q1], u[2 * q1 + 1]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) u[q] = o[q];
+}
+
+__device__ __forceinline__ void team_sync(int team) {
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TEAM) : "memory");
+}
+
+// One transform of the block held as v[m] = x[t + 128 m] (t = thread in the
+// team); leaves v[m] = X[t + 128 m]. E is the team's exchange buffer, tw the
+// table e^{-2 pi i k / N}.
+template <int DIR>
+__device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2 *tw, int t, int team) {
+    // pass 1: R = 16, Ns = 1 (no twiddles)
+    dft16<DIR>(v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) E[pad(16 * t + q)] = v[q];
+    team_sync(team);
+    // pass 2: R = 16, Ns = 16
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = E[pad(t + 128 * m)];
+    team_sync(team);
+    {
+        const int k = t & 15;
+#pragma unroll
+        for (int m = 1; m < 16; ++m) v[m] = ctw<DIR>(v[m], tw[8 * m * k]);
+    }
+    dft16<DIR>(v);
+    {
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) E[pad(base + 16 * q)] = v[q];
+    }
+    team_sync(team);
+    // pass 3: R = 8, Ns = 256; butterflies j = t and j = t + 128
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = t + 128 * h;
+        float2 u[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) u[m] = E[pad(j + 256 * m)];
+#pragma unroll
+        for (int m = 1; m < 8; ++m) u[m] = ctw<DIR>(u[m], tw[m * j]);
+        dft8<DIR>(u);
+        // element j + 256 q = t + 128 (h + 2 q)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[h + 2 * q] = u[q];
+    }
+    team_sync(team);  // the buffer is free for the next pass 1
+}
+
+// FILTER: y = IFFT(Hs * FFT(s)) with Hs = FFT(h) / N; else y = FFT(s).
+template <bool FILTER>
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
+    bf_filter_kernel(const float2 *s, float2 *y, long long n_sig, const float2 *__restrict__ tw_g,
+                     const float2 *__restrict__ H_g) {
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *tw = sm;
+    float2 *Hs = sm + N;
+    const int team = threadIdx.x / TEAM, t = threadIdx.x % TEAM;
+    float2 *E = sm + 2 * N + team * EBUF;
+    for (int i = threadIdx.x; i < N; i += THREADS) {
+        tw[i] = tw_g[i];
+        if (FILTER) {
+            const float2 h = H_g[i];
+            Hs[i] = make_float2(h.x * (1.f / N), h.y * (1.f / N));
+        }
+    }
+    __syncthreads();
+    for (long long q = (long long)blockIdx.x * TEAMS + team; q < n_sig; q += (long long)gridDim.x * TEAMS) {
+        const float2 *sq = s + q * N;
+        float2 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = sq[t + 128 * m];
+        fft2048<-1>(v, E, tw, t, team);
+        if (FILTER) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], Hs[t + 128 * m]);
+            fft2048<1>(v, E, tw, t, team);
+        }
+        float2 *yq = y + q * N;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) yq[t + 128 * m] = v[m];
+    }
+}
+
+}  // namespace bff
+
+using namespace bff;
+
+struct bf_filter_s {
+    int device = 0, sm_count = 0;
+    float2 *tw = nullptr, *H = nullptr, *hpad = nullptr;
+    bool has_taps = false;
+    std::string err;
+    int64_t launches = 0;
+    // host-buffer pipeline: copy-in, compute and copy-out streams, 3 slots
+    cudaStream_t x_in = nullptr, x_run = nullptr, x_out = nullptr;
+    cudaEvent_t x_start = nullptr, x_end = nullptr;
+    cudaEvent_t in_done[3] = {}, run_done[3] = {}, out_done[3] = {};
+    float2 *slot_s[3] = {}, *slot_y[3] = {};
+    size_t slot_cap = 0;  // blocks per slot
+};
+
+static thread_local std::string g_create_err;
+
+static bf_status ff_fail(bf_filter f, bf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    (f ? f->err : g_create_err) = buf;
+    return s;
+}
+
+#define FF_CK(f, call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return ff_fail(f, BF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
+        }                                                                                  \
+    } while (0)
+
+static bf_status ff_device(bf_filter f) {
+    int cur = -1;
+    FF_CK(f, cudaGetDevice(&cur));
+    if (cur != f->device) FF_CK(f, cudaSetDevice(f->device));
+    return BF_OK;
+}
+
+static cudaError_t launch_filter(bool filter, const float2 *s, float2 *y, long long n_sig, const bf_filter f,
+                                 cudaStream_t st) {
+    if (n_sig <= 0) return cudaSuccess;
+    const long long want = (n_sig + TEAMS - 1) / TEAMS;
+    const int grid = (int)std::min<long long>(want, (long long)f->sm_count * CTAS_PER_SM);
+    if (filter)
+        bf_filter_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, f->H);
+    else
+        bf_filter_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, nullptr);
+    return cudaGetLastError();
+}
+
+extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
+    if (!out) return ff_fail(nullptr, BF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n != N) return ff_fail(nullptr, BF_EINVAL, "n = %d: the filter is built for 2048-point transforms", n);
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ff_fail(nullptr, BF_ECUDA, "no usable CUDA device");
+    }
+    if (prop.major < 10) return ff_fail(nullptr, BF_ECUDA, "device sm_%d%d is not a Blackwell part", prop.major,
+                                        prop.minor);
+    bf_filter f = new bf_filter_s();
+    f->device = dev;
+    f->sm_count = prop.multiProcessorCount;
+    // twiddles e^{-2 pi i k / N}, from FP64 values rounded once to FP32
+    std::vector<float2> tw(N);
+    for (int k = 0; k < N; ++k) {
+        const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)N;
+        tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    bool ok = cudaMalloc((void **)&f->tw, N * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc((void **)&f->H, N * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc((void **)&f->hpad, N * sizeof(float2)) == cudaSuccess &&
+              cudaMemcpy(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaFuncSetAttribute(bf_filter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SMEM_BYTES) == cudaSuccess &&
+              cudaFuncSetAttribute(bf_filter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SMEM_BYTES) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&f->x_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&f->x_run, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&f->x_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&f->x_start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&f->x_end, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < 3; ++i)
+        ok = cudaEventCreateWithFlags(&f->in_done[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&f->run_done[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&f->out_done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        bf_filter_destroy(f);
+        return ff_fail(nullptr, BF_ECUDA, "filter allocation or setup failed");
+    }
+    *out = f;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_destroy(bf_filter f) {
+    if (!f) return BF_OK;
+    cudaSetDevice(f->device);
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    for (void *p : {(void *)f->tw, (void *)f->H, (void *)f->hpad})
+        if (p) cudaFree(p);
+    for (int i = 0; i < 3; ++i) {
+        if (f->slot_s[i]) cudaFree(f->slot_s[i]);
+        if (f->slot_y[i]) cudaFree(f->slot_y[i]);
+        for (cudaEvent_t e : {f->in_done[i], f->run_done[i], f->out_done[i]})
+            if (e) cudaEventDestroy(e);
+    }
+    for (cudaEvent_t e : {f->x_start, f->x_end})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : {f->x_in, f->x_run, f->x_out})
+        if (s) cudaStreamDestroy(s);
+    cudaGetLastError();
+    delete f;
+    return BF_OK;
+}
+
+extern "C" const char *bf_filter_last_error(bf_filter f) { return f ? f->err.c_str() : g_create_err.c_str(); }
+
+extern "C" int64_t bf_filter_launch_count(bf_filter f) { return f ? f->launches : 0; }
+
+extern "C" bf_status bf_filter_set_taps(bf_filter f, const void *h_dev, int n_taps, void *stream) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (!h_dev || n_taps < 1 || n_taps > N)
+        return ff_fail(f, BF_EINVAL, "need 1 <= n_taps <= %d and a non-NULL h_dev (n_taps = %d)", N, n_taps);
+    if ((uintptr_t)h_dev & 7u) return ff_fail(f, BF_EINVAL, "h_dev must be 8-byte aligned");
+    bf_status s = ff_device(f);
+    if (s != BF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    FF_CK(f, cudaMemsetAsync(f->hpad, 0, N * sizeof(float2), st));
+    FF_CK(f, cudaMemcpyAsync(f->hpad, h_dev, (size_t)n_taps * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    FF_CK(f, launch_filter(false, f->hpad, f->H, 1, f, st));
+    f->launches++;
+    f->has_taps = true;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_spectrum(bf_filter f, void *H_dev, void *stream) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (!H_dev || ((uintptr_t)H_dev & 7u)) return ff_fail(f, BF_EINVAL, "H_dev must be non-NULL and 8-byte aligned");
+    if (!f->has_taps) return ff_fail(f, BF_ENOTFOUND, "no filter sequence set");
+    bf_status s = ff_device(f);
+    if (s != BF_OK) return s;
+    FF_CK(f, cudaMemcpyAsync(H_dev, f->H, N * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return BF_OK;
+}
+
+static bf_status ff_check_apply(bf_filter f, const void *s, int64_t n_sig, const void *y, bool dev) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (n_sig < 0) return ff_fail(f, BF_EINVAL, "negative n_sig");
+    if (!f->has_taps) return ff_fail(f, BF_ENOTFOUND, "no filter sequence set");
+    if (n_sig == 0) return BF_OK;
+    if (!s || !y) return ff_fail(f, BF_EINVAL, "NULL buffer");
+    if (dev && (((uintptr_t)s & 15u) || ((uintptr_t)y & 15u)))
+        return ff_fail(f, BF_EINVAL, "s_dev and y_dev must be 16-byte aligned");
+    if (s != y) {
+        const uint8_t *a = (const uint8_t *)s, *b = (const uint8_t *)y;
+        const size_t bytes = (size_t)n_sig * N * sizeof(float2);
+        if (a < b + bytes && b < a + bytes) return ff_fail(f, BF_EINVAL, "s and y overlap without being equal");
+    }
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_apply(bf_filter f, const void *s_dev, int64_t n_sig, void *y_dev, void *stream) {
+    bf_status s = ff_check_apply(f, s_dev, n_sig, y_dev, true);
+    if (s != BF_OK || n_sig == 0) return s;
+    if ((s = ff_device(f)) != BF_OK) return s;
+    FF_CK(f, launch_filter(true, (const float2 *)s_dev, (float2 *)y_dev, n_sig, f, (cudaStream_t)stream));
+    f->launches++;
+    return BF_OK;
+}
+
+// Chunks grow from 256 blocks (2 MiB in + 2 MiB out) to 2,048 blocks, so that
+// the first copy-out starts early and later chunks amortise the calls.
+extern "C" bf_status bf_filter_apply_host(bf_filter f, const void *s_host, int64_t n_sig, void *y_host,
+                                          void *stream) {
+    bf_status s = ff_check_apply(f, s_host, n_sig, y_host, false);
+    if (s != BF_OK || n_sig == 0) return s;
+    if ((s = ff_device(f)) != BF_OK) return s;
+    constexpr int64_t FIRST = 256, MAXC = 2048;
+    const size_t need = (size_t)std::min<int64_t>(MAXC, n_sig);
+    if (need > f->slot_cap) {
+        FF_CK(f, cudaDeviceSynchronize());
+        for (int i = 0; i < 3; ++i) {
+            if (f->slot_s[i]) cudaFree(f->slot_s[i]);
+            if (f->slot_y[i]) cudaFree(f->slot_y[i]);
+            f->slot_s[i] = f->slot_y[i] = nullptr;
+        }
+        f->slot_cap = 0;
+        for (int i = 0; i < 3; ++i) {
+            FF_CK(f, cudaMalloc((void **)&f->slot_s[i], need * N * sizeof(float2)));
+            FF_CK(f, cudaMalloc((void **)&f->slot_y[i], need * N * sizeof(float2)));
+        }
+        f->slot_cap = need;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    FF_CK(f, cudaEventRecord(f->x_start, user));
+    FF_CK(f, cudaStreamWaitEvent(f->x_in, f->x_start, 0));
+    FF_CK(f, cudaStreamWaitEvent(f->x_run, f->x_start, 0));
+    FF_CK(f, cudaStreamWaitEvent(f->x_out, f->x_start, 0));
+    const size_t blk = N * sizeof(float2);
+    int64_t done = 0, chunk = FIRST;
+    for (int c = 0; done < n_sig; ++c) {
+        const int k = c % 3;
+        const int64_t nb = std::min<int64_t>(std::min<int64_t>(chunk, (int64_t)f->slot_cap), n_sig - done);
+        if (c >= 3) FF_CK(f, cudaStreamWaitEvent(f->x_in, f->run_done[k], 0));
+        FF_CK(f, cudaMemcpyAsync(f->slot_s[k], (const uint8_t *)s_host + done * blk, nb * blk, cudaMemcpyHostToDevice,
+                                 f->x_in));
+        FF_CK(f, cudaEventRecord(f->in_done[k], f->x_in));
+        FF_CK(f, cudaStreamWaitEvent(f->x_run, f->in_done[k], 0));
+        if (c >= 3) FF_CK(f, cudaStreamWaitEvent(f->x_run, f->out_done[k], 0));
+        FF_CK(f, launch_filter(true, f->slot_s[k], f->slot_y[k], nb, f, f->x_run));
+        f->launches++;
+        FF_CK(f, cudaEventRecord(f->run_done[k], f->x_run));
+        FF_CK(f, cudaStreamWaitEvent(f->x_out, f->run_done[k], 0));
+        FF_CK(f, cudaMemcpyAsync((uint8_t *)y_host + done * blk, f->slot_y[k], nb * blk, cudaMemcpyDeviceToHost,
+                                 f->x_out));
+        FF_CK(f, cudaEventRecord(f->out_done[k], f->x_out));
+        done += nb;
+        chunk = std::min<int64_t>(2 * chunk, MAXC);
+    }
+    FF_CK(f, cudaEventRecord(f->x_end, f->x_out));
+    FF_CK(f, cudaStreamWaitEvent(user, f->x_end, 0));
+    return BF_OK;
+}

@@ -157,3 +157,12 @@ def test_scheduler_empty_and_zero_f(bf):
     assert [t.n_blocks for t in tiles] == [1, 1, 1] and begin == [0, 1, 2, 3]
     tiles, begin = schedule(bf, [3], [], bf.BF_FP32, 0, 4)
     assert tiles == [] and begin == [0, 0]
+
+
+def test_filter_create_rejects_size_before_cuda(bf):
+    L = bf._filter_sigs(bf.lib())
+    h = ctypes.c_void_p()
+    assert L.bf_filter_create(1024, ctypes.byref(h)) == bf.BF_EINVAL and not h.value
+    assert "2048" in bf.bf_filter_last_error(None)
+    assert L.bf_filter_create(2048, None) == bf.BF_EINVAL
+    assert L.bf_filter_destroy(None) == bf.BF_OK

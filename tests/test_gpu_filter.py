@@ -1,0 +1,164 @@
+"""GPU parity of the fast-convolution filter y = IFFT(MULT(FFT(s))) (Sec. III,
+filter equation, Fig. 4; N = 2048) against the FP64 oracle, through the C ABI.
+
+Tolerance: relative Frobenius error <= 1e-5 over the checked signals. An FP32
+radix-16/16/8 transform accumulates about log2(N) * 2^-24 ~ 7e-7 of relative
+rms error per transform; two transforms, the spectrum product and the FP32
+twiddles stay several times below 1e-5, the bound used for every FP32 path.
+Outputs are NaN-poisoned before each run, so unwritten samples fail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1810_11451_gb300 as bf  # noqa: E402
+
+TOL = 1e-5
+N = wl.FILTER_N
+
+
+@pytest.fixture(scope="module")
+def filt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    f = bf.bf_filter_create(N)
+    yield f
+    bf.bf_filter_destroy(f)
+
+
+def dev_c64(a):
+    flat = np.ascontiguousarray(np.asarray(a, dtype=np.complex64)).view(np.float32)
+    return torch.from_numpy(flat.copy()).cuda()
+
+
+def host_c64(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.complex64)
+
+
+def run(filt, h, s, set_taps=True):
+    if set_taps:
+        bf.bf_filter_set_taps(filt, dev_c64(h), len(h))
+    s_d = dev_c64(s)
+    y_d = torch.full_like(s_d, float("nan"))
+    bf.bf_filter_apply(filt, s_d, s.shape[0], y_d)
+    return host_c64(y_d).reshape(s.shape)
+
+
+def rel(y, ref):
+    return float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+
+
+def test_spectrum_matches_definition_dft(filt):
+    b = wl.config_filter_small()
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    H_d = torch.full((2 * N,), float("nan"), device="cuda")
+    bf.bf_filter_spectrum(filt, H_d)
+    H = host_c64(H_d)
+    hp = np.zeros(N, complex)
+    hp[:len(b.h)] = b.h.astype(np.complex64)
+    ref = oracle.dft(hp)
+    assert np.all(np.isfinite(H)) and rel(H, ref) <= TOL
+
+
+def test_small_batch(filt):
+    b = wl.config_filter_small().rounded()
+    y = run(filt, b.h, b.s)
+    assert np.all(np.isfinite(y))
+    e = rel(y, oracle.circular_filter(b.h, b.s))
+    assert e <= TOL, e
+
+
+def test_closed_forms(filt):
+    """h = delta gives y = s; s = delta[n - n0] gives y = h shifted by n0 (with the wrap)."""
+    rng = np.random.default_rng(3)
+    s = (rng.normal(size=(5, N)) + 1j * rng.normal(size=(5, N))).astype(np.complex64)
+    y = run(filt, np.array([1.0 + 0j]), s)
+    assert rel(y, s) <= 1e-6
+    h = wl.config_filter_small().h.astype(np.complex64)
+    imp = np.zeros((4, N), np.complex64)
+    shifts = [0, 1, 1000, N - 1]
+    for i, n0 in enumerate(shifts):
+        imp[i, n0] = 1
+    y = run(filt, h, imp)
+    hp = np.zeros(N, np.complex64)
+    hp[:len(h)] = h
+    for i, n0 in enumerate(shifts):
+        assert rel(y[i], np.roll(hp, n0)) <= TOL
+
+
+@pytest.mark.parametrize("n_sig", [1, 3, 607, 1001])
+def test_ragged_counts(filt, n_sig):
+    """Odd counts leave one team idle; counts above the resident grid (2 teams
+    x 2 CTAs x SMs) make teams loop; every signal is checked."""
+    rng = np.random.default_rng(n_sig)
+    b = wl.config_filter_small()
+    s = (rng.normal(size=(n_sig, N)) + 1j * rng.normal(size=(n_sig, N))).astype(np.complex64)
+    y = run(filt, b.h.astype(np.complex64), s)
+    idx = np.arange(n_sig) if n_sig <= 8 else np.unique(np.linspace(0, n_sig - 1, 8).astype(int))
+    ref = oracle.circular_filter(b.h.astype(np.complex64), s[idx])
+    assert np.all(np.isfinite(y)) and rel(y[idx], ref) <= TOL
+
+
+def test_full_size_sampled(filt):
+    """The bench workload (16 slots x 64 antennas x 14 symbols = 14,336 blocks)
+    in the bench's launch form; 48 blocks spread over the batch against the oracle."""
+    b = wl.config_filter_bench().rounded()
+    y = run(filt, b.h, b.s)
+    assert np.all(np.isfinite(y))
+    idx = np.unique(np.linspace(0, b.n_sig - 1, 48).astype(int))
+    assert rel(y[idx], oracle.circular_filter(b.h, b.s[idx])) <= TOL
+
+
+def test_in_place_host_and_determinism(filt):
+    b = wl.config_filter_tti().rounded()
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    s_d = dev_c64(b.s)
+    y1 = torch.empty_like(s_d)
+    bf.bf_filter_apply(filt, s_d, b.n_sig, y1)
+    y2 = torch.empty_like(s_d)
+    bf.bf_filter_apply(filt, s_d, b.n_sig, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1.view(torch.int32), y2.view(torch.int32))
+    inplace = s_d.clone()
+    bf.bf_filter_apply(filt, inplace, b.n_sig, inplace)
+    s_h = torch.from_numpy(np.ascontiguousarray(b.s.astype(np.complex64)).view(np.float32).copy()).pin_memory()
+    y_h = torch.full_like(s_h, float("nan")).pin_memory()
+    bf.bf_filter_apply_host(filt, s_h, b.n_sig, y_h)
+    torch.cuda.synchronize()
+    assert torch.equal(inplace.view(torch.int32), y1.view(torch.int32))
+    assert torch.equal(y_h.view(torch.int32), y1.cpu().view(torch.int32))
+
+
+def test_errors(filt):
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_filter_create(1024)
+    assert ei.value.status == bf.BF_EINVAL
+    h = dev_c64(np.ones(4))
+    for n_taps in (0, N + 1):
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_filter_set_taps(filt, h, n_taps)
+        assert ei.value.status == bf.BF_EINVAL
+    f2 = bf.bf_filter_create(N)
+    try:
+        s = dev_c64(np.ones((2, N))).view(-1)  # flat float32 view of two blocks
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_filter_apply(f2, s, 2, s)
+        assert ei.value.status == bf.BF_ENOTFOUND
+        bf.bf_filter_set_taps(f2, h, 4)
+        with pytest.raises(bf.BfError) as ei:  # overlapping (16 bytes apart) but not equal
+            bf.bf_filter_apply(f2, s, 1, s[4:])
+        assert ei.value.status == bf.BF_EINVAL and "overlap" in str(ei.value)
+        out = torch.empty_like(s)
+        with pytest.raises(bf.BfError) as ei:  # 8-byte aligned only
+            bf.bf_filter_apply(f2, s[2:], 1, out)
+        assert ei.value.status == bf.BF_EINVAL and "aligned" in str(ei.value)
+        bf.bf_filter_apply(f2, s, 0, s)  # no-op
+    finally:
+        bf.bf_filter_destroy(f2)
