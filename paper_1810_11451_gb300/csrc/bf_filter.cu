@@ -15,6 +15,11 @@
 // The last inverse pass writes y in natural order, coalesced.
 //
 // The 1/N of the inverse is folded into the spectrum (a power of two, exact).
+// Shared-memory bandwidth bounds this kernel, so each pass loads only one or
+// two twiddles per butterfly and forms the others by complex products of at
+// most three factors: pass 2 loads w = e^{-2 pi i k / 256} and w^4 (k = t mod
+// 16, at k and 16 + k), pass 3 loads w = e^{-2 pi i j / 2048} (at TW3 + j).
+// The tables are laid out in thread order, so a warp reads consecutive words.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,24 +36,51 @@ namespace bff {
 
 constexpr int N = 2048;
 constexpr int TEAM = 128;                 // threads per block of samples
-// Teams per CTA and CTAs per SM (compile-time knobs): 2 x 2 keeps the
+// Teams per CTA and CTAs per SM (compile-time knobs): 4 x 1 keeps the
 // transform's 16 values per thread and its temporaries in registers.
 #ifndef BF_FILTER_TEAMS
-#define BF_FILTER_TEAMS 2
+#define BF_FILTER_TEAMS 4
 #endif
 #ifndef BF_FILTER_CTAS
-#define BF_FILTER_CTAS 2
+#define BF_FILTER_CTAS 1
+#endif
+// Prefetch: while a team transforms one block, cp.async copies its next
+// block into a shared-memory staging buffer.
+#ifndef BF_FILTER_PREFETCH
+#define BF_FILTER_PREFETCH 1
 #endif
 constexpr int TEAMS = BF_FILTER_TEAMS;
+constexpr bool PREFETCH = BF_FILTER_PREFETCH != 0;
 constexpr int THREADS = TEAM * TEAMS;
 constexpr int CTAS_PER_SM = BF_FILTER_CTAS;
 constexpr int EBUF = N + N / 16;          // padded exchange buffer (complex values)
-constexpr int SMEM_BYTES = (2 * N + TEAMS * EBUF) * 8;
+constexpr int TW3 = 32;                   // start of the pass-3 twiddles
+constexpr int TW_SIZE = TW3 + 256;        // 288 values
+static_assert(TW_SIZE <= N, "twiddle table fits its shared-memory slot");
+constexpr int TEAM_SMEM = EBUF + (PREFETCH ? N : 0);  // exchange (+ staging) buffer per team
+constexpr int SMEM_BYTES = (2 * N + TEAMS * TEAM_SMEM) * 8;
 
 __host__ __device__ constexpr int pad(int e) { return e + (e >> 4); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums as packed FP32 pairs (one instruction each on sm_100 and up):
+// the butterflies are mostly additions and the kernel is issue-bound.
+#ifndef BF_FILTER_PACKED
+#define BF_FILTER_PACKED 1
+#endif
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if BF_FILTER_PACKED
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if BF_FILTER_PACKED
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -136,13 +168,27 @@ __device__ __forceinline__ void dft8(float2 (&u)[8]) {
     for (int q = 0; q < 8; ++q) u[q] = o[q];
 }
 
+// The team's copy of one block (16 KB) into shared memory: 8 asynchronous
+// 16-byte copies per thread, one commit group.
+__device__ __forceinline__ void prefetch_block(float2 *dst, const float2 *src, int t) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int off = (t + TEAM * i) * 16;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + off), "l"(g + off) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void prefetch_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void team_sync(int team) {
     asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TEAM) : "memory");
 }
 
 // One transform of the block held as v[m] = x[t + 128 m] (t = thread in the
 // team); leaves v[m] = X[t + 128 m]. E is the team's exchange buffer, tw the
-// table e^{-2 pi i k / N}.
+// per-pass twiddle table.
 template <int DIR>
 __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2 *tw, int t, int team) {
     // pass 1: R = 16, Ns = 1 (no twiddles)
@@ -156,8 +202,21 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
     team_sync(team);
     {
         const int k = t & 15;
+        const float2 w1 = tw[k], w4 = tw[16 + k];
+        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+        float2 p = w4;  // w^(4a)
 #pragma unroll
-        for (int m = 1; m < 16; ++m) v[m] = ctw<DIR>(v[m], tw[8 * m * k]);
+        for (int a = 0; a < 4; ++a) {
+            if (a >= 2) p = cmul(p, w4);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int m = 4 * a + b;
+                if (m == 0) continue;
+                const float2 wb = b == 1 ? w1 : (b == 2 ? w2 : w3);
+                const float2 w = a == 0 ? wb : (b == 0 ? p : cmul(p, wb));
+                v[m] = ctw<DIR>(v[m], w);
+            }
+        }
     }
     dft16<DIR>(v);
     {
@@ -173,8 +232,14 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
         float2 u[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) u[m] = E[pad(j + 256 * m)];
-#pragma unroll
-        for (int m = 1; m < 8; ++m) u[m] = ctw<DIR>(u[m], tw[m * j]);
+        const float2 w1 = tw[TW3 + j], w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
+        u[1] = ctw<DIR>(u[1], w1);
+        u[2] = ctw<DIR>(u[2], w2);
+        u[3] = ctw<DIR>(u[3], w3);
+        u[4] = ctw<DIR>(u[4], w4);
+        u[5] = ctw<DIR>(u[5], cmul(w4, w1));
+        u[6] = ctw<DIR>(u[6], cmul(w4, w2));
+        u[7] = ctw<DIR>(u[7], cmul(w4, w3));
         dft8<DIR>(u);
         // element j + 256 q = t + 128 (h + 2 q)
 #pragma unroll
@@ -192,20 +257,33 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     float2 *tw = sm;
     float2 *Hs = sm + N;
     const int team = threadIdx.x / TEAM, t = threadIdx.x % TEAM;
-    float2 *E = sm + 2 * N + team * EBUF;
+    float2 *E = sm + 2 * N + team * TEAM_SMEM;
+    float2 *IN = E + EBUF;  // staging buffer (PREFETCH only)
     for (int i = threadIdx.x; i < N; i += THREADS) {
-        tw[i] = tw_g[i];
+        if (i < TW_SIZE) tw[i] = tw_g[i];
         if (FILTER) {
             const float2 h = H_g[i];
             Hs[i] = make_float2(h.x * (1.f / N), h.y * (1.f / N));
         }
     }
     __syncthreads();
-    for (long long q = (long long)blockIdx.x * TEAMS + team; q < n_sig; q += (long long)gridDim.x * TEAMS) {
-        const float2 *sq = s + q * N;
+    const long long stride = (long long)gridDim.x * TEAMS;
+    long long q = (long long)blockIdx.x * TEAMS + team;
+    if (PREFETCH && q < n_sig) prefetch_block(IN, s + q * N, t);
+    for (; q < n_sig; q += stride) {
         float2 v[16];
+        if (PREFETCH) {
+            prefetch_wait();
+            team_sync(team);  // every thread's copies of block q have landed
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = sq[t + 128 * m];
+            for (int m = 0; m < 16; ++m) v[m] = IN[t + 128 * m];
+            team_sync(team);  // all reads done before the next copy overwrites IN
+            if (q + stride < n_sig) prefetch_block(IN, s + (q + stride) * N, t);
+        } else {
+            const float2 *sq = s + q * N;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = sq[t + 128 * m];
+        }
         fft2048<-1>(v, E, tw, t, team);
         if (FILTER) {
 #pragma unroll
@@ -291,12 +369,17 @@ extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
     bf_filter f = new bf_filter_s();
     f->device = dev;
     f->sm_count = prop.multiProcessorCount;
-    // twiddles e^{-2 pi i k / N}, from FP64 values rounded once to FP32
-    std::vector<float2> tw(N);
-    for (int k = 0; k < N; ++k) {
-        const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)N;
-        tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    // per-pass twiddles e^{-2 pi i e / N}, from FP64 values rounded once to FP32
+    std::vector<float2> tw(N, make_float2(0.f, 0.f));
+    auto root = [](int e) {
+        const double a = 2.0 * 3.14159265358979323846 * (double)(e % N) / (double)N;
+        return make_float2((float)std::cos(a), (float)-std::sin(a));
+    };
+    for (int k = 0; k < 16; ++k) {
+        tw[k] = root(8 * k);        // e^{-2 pi i k / 256}
+        tw[16 + k] = root(32 * k);  // e^{-2 pi i 4 k / 256}
     }
+    for (int j = 0; j < 256; ++j) tw[TW3 + j] = root(j);  // e^{-2 pi i j / 2048}
     bool ok = cudaMalloc((void **)&f->tw, N * sizeof(float2)) == cudaSuccess &&
               cudaMalloc((void **)&f->H, N * sizeof(float2)) == cudaSuccess &&
               cudaMalloc((void **)&f->hpad, N * sizeof(float2)) == cudaSuccess &&
