@@ -502,6 +502,8 @@ def main():
     ap.add_argument("--sets", type=int, default=3, help="rotating buffer sets (3 keeps the working set above L2)")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven, reduced-precision and serving legs")
     ap.add_argument("--serving-ttis", type=int, default=20000, help="TTIs of the split-bf16 serving run")
+    ap.add_argument("--legs", default="fused_output,uneven,reduced,filter,serving",
+                    help="comma-separated secondary workloads to run after the headline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -560,9 +562,10 @@ def main():
     # ---- CPU baseline (oracle), which also gives the references for accuracy
     cpu, acc, refs, ref_full = None, None, {}, None
     extra = not args.no_extra and rank == 0
-    b_uneven = wl.config_uneven() if extra else None
-    b_reduced = wl.config_reduced() if extra else None
-    b_filter = wl.config_filter_bench() if extra else None
+    want = set(x.strip() for x in args.legs.split(",") if x.strip())
+    b_uneven = wl.config_uneven() if extra and "uneven" in want else None
+    b_reduced = wl.config_reduced() if extra and "reduced" in want else None
+    b_filter = wl.config_filter_bench() if extra and "filter" in want else None
     filter_sample = None
     if rank == 0 and not args.no_cpu:
         cpu, ref = cpu_baseline(batch)
@@ -585,17 +588,21 @@ def main():
 
     # ---- the other workloads: uneven batching, reduced precision, serving
     legs = {}
-    if extra:
+    if extra and "fused_output" in want:
         legs["fused_output"] = fused_output_leg(torch, bf, plan, batch, ref_full, stream)
-        ref_full = None
+    ref_full = None
+    if b_uneven is not None:
         ref_d = to_device_ref(torch, refs.pop("uneven", None))
         legs["uneven"] = uneven_leg(torch, bf, plan, b_uneven, ref_d, stream)
         del ref_d
+    if b_reduced is not None:
         ref_d = to_device_ref(torch, refs.pop("reduced", None))
         legs["reduced"] = reduced_leg(torch, bf, plan, b_reduced, ref_d, stream)
         del ref_d
         torch.cuda.empty_cache()
+    if b_filter is not None:
         legs["filter"] = filter_leg(torch, bf, b_filter, filter_sample, stream)
+    if extra and "serving" in want:
         legs["serving_bf16x3"] = serving_leg(torch, bf, args.serving_ttis, bf.BF_BF16X3)
         legs["serving_fp32"] = serving_leg(torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
     status = bf.bf_device_status(plan)

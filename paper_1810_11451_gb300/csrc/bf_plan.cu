@@ -367,59 +367,78 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
         total += cost[g] * groups[g].n_blocks;
         n_blocks += groups[g].n_blocks;
     }
-    wl.tiles.clear();
-    wl.cta_begin.clear();
+    wl.n_tiles = 0;
     if (n_blocks == 0) {  // nothing to launch: one empty range
         wl.cta_begin.assign(2, 0);
         return;
     }
     const int n_cta = (int)std::max<int64_t>(1, std::min<int64_t>(max_cta, n_blocks));
-    wl.tiles.reserve((size_t)n_blocks);
-    wl.cta_begin.reserve((size_t)n_cta + 1);
-    wl.cta_begin.push_back(0);
-    // midpoint rule: block k goes to CTA floor((cum + cost/2) / (total / n_cta)),
-    // clamped so that ranges stay contiguous and no CTA is left empty
-    const double per_cost = total > 0 ? n_cta / total : 0.0;
-    double cum = 0;
-    int cur = 0, blk = 0;
+    // Midpoint rule: block k goes to CTA floor((cum_k + cost_k / 2) * n_cta /
+    // total), so CTA c starts at the first block whose midpoint reaches
+    // c * total / n_cta. One walk over the groups finds every start; then the
+    // starts are made strictly increasing and leave every CTA a block.
+    std::vector<int64_t> &bound = wl.bound;
+    bound.assign(n_cta + 1, 0);
+    bound[n_cta] = n_blocks;
+    {
+        int g = 0;
+        double c0 = 0;  // cost before group g
+        int64_t k0 = 0; // blocks before group g
+        for (int c = 1; c < n_cta; ++c) {
+            const double target = total * c / n_cta;
+            while (g < n_groups && c0 + cost[g] * (groups[g].n_blocks - 0.5) < target) {
+                c0 += cost[g] * groups[g].n_blocks;
+                k0 += groups[g].n_blocks;
+                ++g;
+            }
+            int64_t b = 0;
+            if (g < n_groups && cost[g] > 0) {
+                b = (int64_t)std::ceil((target - c0) / cost[g] - 0.5);
+                b = std::min<int64_t>(std::max<int64_t>(b, 0), groups[g].n_blocks);
+            }
+            bound[c] = k0 + b;
+        }
+        for (int c = 1; c < n_cta; ++c) bound[c] = std::max(bound[c], bound[c - 1] + 1);
+        for (int c = n_cta - 1; c >= 1; --c) bound[c] = std::min(bound[c], bound[c + 1] - 1);
+    }
+    // tiles: each group's blocks, cut at the range starts, in runs of up to
+    // tile_blocks (at most one tile per block, so the arrays are sized once)
+    if (wl.tiles.size() < (size_t)n_blocks) wl.tiles.resize((size_t)n_blocks);
+    wl.cta_begin.resize((size_t)n_cta + 1);
+    Tile *tiles = wl.tiles.data();
+    int32_t *cta_begin = wl.cta_begin.data();
+    const int64_t *bnd = bound.data();
+    int n_tiles = 0;
+    cta_begin[0] = 0;
+    int cur = 0;
     int64_t k = 0;
+    int blk = 0;
     for (int g = 0; g < n_groups; ++g) {
         const bf_group &gr = groups[g];
         const int f = f_slot[gr.prec_id];
         const int64_t sb = held ? held_block_bytes(f, prec == BF_BF16X3 ? 2 : 1) : (int64_t)f * S_BYTES_PER_F;
         const int tile_blocks = tune.tile_blocks_for(prec, f);
-        int open = -1;  // index of the tile being filled (this group, this CTA)
-        for (int b = 0; b < gr.n_blocks; ++b, ++k) {
-            int c = (int)((cum + 0.5 * cost[g]) * per_cost);
-            const int lo = (int)std::max<int64_t>(cur, n_cta - (n_blocks - k));
-            const int hi = std::min(k > 0 ? cur + 1 : 0, n_cta - 1);
-            c = std::min(std::max(c, lo), hi);
-            if (c != cur) {
-                cur = c;
-                wl.cta_begin.push_back((int32_t)wl.tiles.size());
-                open = -1;
+        int pos = 0;
+        while (pos < gr.n_blocks) {
+            while (cur + 1 < n_cta && bnd[cur + 1] <= k + pos) cta_begin[++cur] = n_tiles;  // a range starts here
+            const int stop = cur + 1 < n_cta ? (int)std::min<int64_t>(gr.n_blocks, bnd[cur + 1] - k) : gr.n_blocks;
+            for (int b = pos; b < stop; b += tile_blocks) {
+                Tile &t = tiles[n_tiles++];
+                t.s_off = gr.s_off + (int64_t)b * sb;
+                t.r_off = gr.r_off + (int64_t)b * r_block_stride;
+                t.prec = gr.prec_id;
+                t.sblk = blk + b;
+                t.f = (int16_t)f;
+                t.nblk = (int16_t)std::min(tile_blocks, stop - b);
+                t.flags = 0;
             }
-            cum += cost[g];
-            if (open >= 0 && wl.tiles[open].nblk < tile_blocks) {
-                ++wl.tiles[open].nblk;
-                continue;
-            }
-            Tile t;
-            t.s_off = gr.s_off + (int64_t)b * sb;
-            t.r_off = gr.r_off + (int64_t)b * r_block_stride;
-            t.prec = gr.prec_id;
-            t.sblk = blk + b;
-            t.f = (int16_t)f;
-            t.nblk = 1;
-            t.flags = 0;
-            open = (int)wl.tiles.size();
-            wl.tiles.push_back(t);
+            pos = stop;
         }
+        k += gr.n_blocks;
         blk += gr.n_blocks;
     }
-    const int n_tiles = (int)wl.tiles.size();
-    wl.cta_begin.push_back(n_tiles);
-    Tile *tiles = wl.tiles.data();
+    wl.n_tiles = n_tiles;
+    cta_begin[n_cta] = n_tiles;
     // precoder-run flags within each CTA's range (tiles with f > 0 only)
     for (int c = 0; c + 1 < (int)wl.cta_begin.size(); ++c) {
         int prev = -1;
@@ -452,7 +471,7 @@ extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const 
     static thread_local WorkList wl;  // reused: repeated calls allocate nothing
     const TuneTable tune;
     build_worklist(f_of_slot, tune, groups, n_groups, prec, held != 0, max_cta, R_BLOCK_BYTES, wl);
-    const int nt = (int)wl.tiles.size();
+    const int nt = wl.n_tiles;
     *n_cta_out = (int32_t)wl.cta_begin.size() - 1;
     if (!tiles_out) return nt;  // size query
     if (nt > max_tiles || !cta_begin_out) return -BF_EINVAL;
@@ -537,9 +556,9 @@ bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const b
     WorkList &wl = plan->scratch_wl;
     build_worklist(plan->f_slot.data(), plan->tune, groups, n_groups, prec, held,
                    max_cta > 0 ? max_cta : max_cta_for(plan, prec), r_block_stride_of(layout), wl);
-    if (wl.tiles.empty()) return BF_OK;
+    if (wl.n_tiles == 0) return BF_OK;
     bf_status s;
-    const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
+    const size_t tb = (size_t)wl.n_tiles * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
     const size_t bytes = tb + cb;
     // reuse an entry that already holds exactly this list
     WorkBuf *hit = nullptr;
@@ -615,8 +634,8 @@ extern "C" bf_status bf_batch_create_rl(bf_plan plan, const void *S_dev, const f
                    max_cta_for(plan, prec), r_block_stride_of(layout), wl);
     bf_batch bt = new bf_batch_s();
     bt->plan = plan;
-    const size_t tb = wl.tiles.size() * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
-    if (!wl.tiles.empty()) {
+    const size_t tb = (size_t)wl.n_tiles * sizeof(Tile), cb = wl.cta_begin.size() * sizeof(int32_t);
+    if (wl.n_tiles > 0) {
         if (cudaMalloc((void **)&bt->d, tb + cb) != cudaSuccess) {
             cudaGetLastError();
             delete bt;
@@ -630,7 +649,7 @@ extern "C" bf_status bf_batch_create_rl(bf_plan plan, const void *S_dev, const f
         }
     }
     bt->p = make_params(plan, bt->d, tb, S_dev, scale_dev, R_dev, prec, layout);
-    bt->n_cta = wl.tiles.empty() ? 0 : (int)wl.cta_begin.size() - 1;
+    bt->n_cta = wl.n_tiles == 0 ? 0 : (int)wl.cta_begin.size() - 1;
     bt->prec = prec;
     bt->held = scale_dev != nullptr;
     cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);

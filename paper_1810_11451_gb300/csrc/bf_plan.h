@@ -41,9 +41,11 @@ struct TuneTable {
 };
 
 struct WorkList {
-    std::vector<Tile> tiles;
+    std::vector<Tile> tiles;      // capacity kept across calls; the first n_tiles are valid
+    int n_tiles = 0;
     std::vector<int32_t> cta_begin;
-    std::vector<double> cost;  // scheduling cost per tile (scratch)
+    std::vector<double> cost;     // scheduling cost of one block, per group (scratch)
+    std::vector<int64_t> bound;   // first block of each CTA's range (scratch)
 };
 
 // One work-list buffer of the ring: pinned host image, device copy, and the

@@ -93,10 +93,10 @@ def test_closed_forms(filt):
         assert rel(y[i], np.roll(hp, n0)) <= TOL
 
 
-@pytest.mark.parametrize("n_sig", [1, 3, 607, 1001])
+@pytest.mark.parametrize("n_sig", [1, 3, 607, 1001, 2000])
 def test_ragged_counts(filt, n_sig):
-    """Odd counts leave one team idle; counts above the resident grid (2 teams
-    x 2 CTAs x SMs) make teams loop; every signal is checked."""
+    """Counts that leave teams idle, and counts above the number of resident
+    teams that make teams loop; sampled signals are checked."""
     rng = np.random.default_rng(n_sig)
     b = wl.config_filter_small()
     s = (rng.normal(size=(n_sig, N)) + 1j * rng.normal(size=(n_sig, N))).astype(np.complex64)
