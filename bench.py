@@ -529,6 +529,8 @@ def main():
     stream = torch.cuda.current_stream()
     best = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_BF16X3, R_sets[s]) for s in range(n_sets)}
     plain = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_FP32, R_sets[s]) for s in range(n_sets)}
+    plain3 = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_FP32_3M, R_sets[s])
+              for s in range(n_sets)}
     handles = [best[s] for s in range(n_sets)]
     flops = batch.flops()
     alg_bytes = batch.algorithmic_bytes()
@@ -549,10 +551,11 @@ def main():
 
     # ---- the plain FP32 form on the same GPU
     k2 = max(50, args.steps // 10)
-    p_ms = float("nan")
+    p_ms = p3_ms = float("nan")
     if not args.no_plain:
         p_total = time_launches(torch, bf, [plain[s] for s in range(n_sets)], k2, args.warmup, stream)
         p_ms = p_total / k2
+        p3_ms = time_launches(torch, bf, [plain3[s] for s in range(n_sets)], k2, args.warmup, stream) / k2
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -575,7 +578,7 @@ def main():
         ref_full = refs.pop("fullband")
         Rref_d = to_device_ref(torch, ref_full)
         acc = {}
-        for name, h in (("bf16x3", best[0]), ("fp32", plain[0])):
+        for name, h in (("bf16x3", best[0]), ("fp32", plain[0]), ("fp32_3m", plain3[0])):
             bf.bf_batch_launch(h, stream)
             num, den = bf.bf_errnorm(plan, R_sets[0], Rref_d, lay.r_blocks, None, stream)
             acc[name] = float(np.sqrt(num / den))
@@ -583,6 +586,7 @@ def main():
     for s in range(n_sets):
         bf.bf_batch_destroy(best[s])
         bf.bf_batch_destroy(plain[s])
+        bf.bf_batch_destroy(plain3[s])
     del S_sets, R_sets
     torch.cuda.empty_cache()
 
@@ -620,6 +624,8 @@ def main():
         "fp32_plain": {"value": world * flops / (p_ms * 1e-3) / 1e9 if p_ms == p_ms else None, "unit": UNIT, "ms_per_step": p_ms,
                        "kernel_ms": p_ms,
                        "blocks_per_s": world * batch.total_blocks / (p_ms * 1e-3)},
+        "fp32_3m": {"value": world * flops / (p3_ms * 1e-3) / 1e9 if p3_ms == p3_ms else None, "unit": UNIT,
+                    "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add"},
         "speedup_vs_fp32_plain": p_ms / ms_step if p_ms == p_ms else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_for("bf_tc.cu"),

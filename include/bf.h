@@ -52,6 +52,11 @@ typedef enum {
 /* Arithmetic of the product. All forms accumulate in FP32 and write complex64 R
  * (or the type a bf_rlayout names).
  *  BF_FP32   : plain form, FP32 fused multiply-add on the CUDA cores; S complex64.
+ *  BF_FP32_3M: FP32 on the CUDA cores with three real products per complex
+ *              multiply-add instead of four: per output element
+ *              P1 = sum Re W Re S, P2 = sum Im W Im S,
+ *              P3 = sum (Re W + Im W)(Re S + Im S),
+ *              Re R = P1 - P2, Im R = (P3 - P1) - P2; S complex64.
  *  BF_BF16   : single-pass tensor-core form, operands rounded to bfloat16.
  *  BF_FP16   : single-pass tensor-core form, operands rounded to binary16.
  *  BF_BF16X3 : split form, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
@@ -59,7 +64,7 @@ typedef enum {
  * The tensor-core forms take S either as complex64 (converted on chip, no
  * per-block scale) or "held": pre-encoded by bf_quantize_symbols with one
  * power-of-two scale per block. W is always taken from the plan's images. */
-typedef enum { BF_FP32 = 0, BF_BF16 = 1, BF_FP16 = 2, BF_BF16X3 = 3 } bf_precision;
+typedef enum { BF_FP32 = 0, BF_BF16 = 1, BF_FP16 = 2, BF_BF16X3 = 3, BF_FP32_3M = 4 } bf_precision;
 
 /* One group: n_blocks consecutive blocks that all multiply precoder prec_id.
  * s_off / r_off are BYTE offsets of the group's first block in the S and R
@@ -121,7 +126,7 @@ bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_hos
 
 /* Bytes of one held (pre-encoded) S block for precision prec at f flows:
  * terms * 128 * K, K = 2f rounded up to a multiple of 16, terms = 2 for
- * BF_BF16X3 and 1 for BF_BF16 / BF_FP16; 0 for BF_FP32 or f out of range.
+ * BF_BF16X3 and 1 for BF_BF16 / BF_FP16; 0 for the FP32 forms or f out of range.
  * Layout of a term: 64 rows (resource element j; rows 60..63 are zero) by K
  * columns (column 2k = Re S[k][j], 2k+1 = Im S[k][j], zero beyond 2f), stored
  * as 8x8 tiles of 16-bit values: element (row, col) at byte

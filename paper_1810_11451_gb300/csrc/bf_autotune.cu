@@ -70,7 +70,7 @@ bf_status time_batch(bf_plan plan, const Scratch &sc, bf_precision prec, int f, 
 
 extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) {
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
-    if (prec < BF_FP32 || prec > BF_BF16X3) return bf_fail(plan, BF_EINVAL, "unknown precision");
+    if (prec < BF_FP32 || prec >= N_PREC) return bf_fail(plan, BF_EINVAL, "unknown precision");
     bf_status s = plan_ensure_device(plan);
     if (s != BF_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -120,8 +120,8 @@ extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) 
         T.tile_blocks[p][b] = best_tb;
         T.ns_per_block[p][b] = best_slope;
     }
-    if (result == BF_OK && prec == BF_FP32) {
-        // CTAs per SM of the CUDA-core kernel, at f = 36
+    if (result == BF_OK && simt_form(prec)) {
+        // CTAs per SM of the CUDA-core kernels (shared by both forms), at f = 36
         double best = 1e30;
         int best_c = T.simt_ctas_per_sm;
         for (int c = 1; c <= plan->simt_resident; ++c) {
@@ -145,7 +145,7 @@ extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) 
 
 extern "C" bf_status bf_tune_query(bf_plan plan, bf_precision prec, int32_t f, double *ns_per_block,
                                    int32_t *tile_blocks, int32_t *tuned) {
-    if (!plan || prec < BF_FP32 || prec > BF_BF16X3 || f < 0 || f > F_LIMIT)
+    if (!plan || prec < BF_FP32 || prec >= N_PREC || f < 0 || f > F_LIMIT)
         return bf_fail(plan, BF_EINVAL, "bad arguments");
     const TuneTable &T = plan->tune;
     if (ns_per_block) *ns_per_block = T.ns_per_block[prec][f_bucket(f)];
@@ -162,12 +162,12 @@ extern "C" bf_status bf_tune_save(bf_plan plan, const char *path) {
     fprintf(fh, "{\n  \"format\": \"libbf-tune-1\",\n  \"sm_count\": %d,\n  \"simt_ctas_per_sm\": %d,\n",
             plan->sm_count, T.simt_ctas_per_sm);
     fprintf(fh, "  \"f_bucket_upper\": [0, 8, 16, 24, 36],\n  \"precisions\": [\n");
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < N_PREC; ++p) {
         fprintf(fh, "    {\"precision\": %d, \"tuned\": %d, \"ns_per_block\": [", p, T.tuned[p] ? 1 : 0);
         for (int b = 0; b < TUNE_BUCKETS; ++b) fprintf(fh, "%s%.6f", b ? ", " : "", T.ns_per_block[p][b]);
         fprintf(fh, "], \"tile_blocks\": [");
         for (int b = 0; b < TUNE_BUCKETS; ++b) fprintf(fh, "%s%d", b ? ", " : "", T.tile_blocks[p][b]);
-        fprintf(fh, "]}%s\n", p < 3 ? "," : "");
+        fprintf(fh, "]}%s\n", p < N_PREC - 1 ? "," : "");
     }
     fprintf(fh, "  ]\n}\n");
     const bool ok = fclose(fh) == 0;
@@ -191,11 +191,14 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
     if (pos == std::string::npos || sscanf(txt.c_str() + pos + 19, "%d", &T.simt_ctas_per_sm) != 1 ||
         T.simt_ctas_per_sm < 1 || T.simt_ctas_per_sm > 16)
         return bad("simt_ctas_per_sm");
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < N_PREC; ++p) {
         char key[32];
         snprintf(key, sizeof key, "\"precision\": %d,", p);
         pos = txt.find(key);
-        if (pos == std::string::npos) return bad("missing precision");
+        if (pos == std::string::npos) {
+            if (p == BF_FP32_3M) continue;  // tables written before that form existed
+            return bad("missing precision");
+        }
         int tuned = 0;
         size_t q = txt.find("\"tuned\":", pos);
         if (q == std::string::npos || sscanf(txt.c_str() + q + 8, "%d", &tuned) != 1) return bad("tuned");

@@ -28,13 +28,20 @@ __host__ __device__ constexpr int64_t held_block_bytes(int f, int terms) {
     return (int64_t)terms * 64 * kpad_of(f) * 2;
 }
 
-// FP32 precoder image for the CUDA-core kernel: planar, flow-major,
-// Re W[i][k] at float index k*64 + i, Im W[i][k] at f*64 + k*64 + i.
-__host__ __device__ constexpr int simt_img_bytes(int f) { return 2 * N_ANT * f * 4; }
-constexpr int SIMT_IMG_MAX = simt_img_bytes(F_LIMIT);  // 18,432
+// Precisions: the four tensor-core / CUDA-core forms and the three-product
+// CUDA-core form (BF_FP32_3M).
+constexpr int N_PREC = 5;
+__host__ __device__ constexpr bool simt_form(int prec) { return prec == BF_FP32 || prec == BF_FP32_3M; }
+
+// FP32 precoder image for the CUDA-core kernels: planar, flow-major,
+// Re W[i][k] at float index k*64 + i, Im W[i][k] at f*64 + k*64 + i, and
+// Re W + Im W (rounded to FP32) at 2*f*64 + k*64 + i for the three-product form.
+__host__ __device__ constexpr int simt_img_bytes(int f, int planes = 2) { return planes * N_ANT * f * 4; }
+constexpr int SIMT_IMG_MAX = simt_img_bytes(F_LIMIT);      // 18,432
+constexpr int SIMT3_IMG_MAX = simt_img_bytes(F_LIMIT, 3);  // 27,648
 
 // Per-slot strides of the precoder store.
-constexpr int64_t W_SIMT_STRIDE = SIMT_IMG_MAX;
+constexpr int64_t W_SIMT_STRIDE = SIMT3_IMG_MAX;
 constexpr int64_t W_BF16X2_STRIDE = 2 * TC_IMG_MAX;  // hi image then lo image, compact
 constexpr int64_t W_FP16_STRIDE = TC_IMG_MAX;
 

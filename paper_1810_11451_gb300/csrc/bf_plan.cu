@@ -461,7 +461,7 @@ extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const 
                                bf_precision prec, int32_t held, int32_t max_cta, bf_tile *tiles_out,
                                int32_t max_tiles, int32_t *cta_begin_out, int32_t *n_cta_out) {
     if (!f_of_slot || n_slots < 0 || n_groups < 0 || (n_groups && !groups) || max_cta < 1 || !n_cta_out ||
-        prec < BF_FP32 || prec > BF_BF16X3 || (held && prec == BF_FP32))
+        prec < BF_FP32 || prec >= N_PREC || (held && simt_form(prec)))
         return -BF_EINVAL;
     for (int g = 0; g < n_groups; ++g) {
         if (groups[g].prec_id < 0 || groups[g].prec_id >= n_slots || groups[g].n_blocks < 0) return -BF_EINVAL;
@@ -494,8 +494,9 @@ static bf_status validate_apply(bf_plan plan, const void *S, const float *scale,
                                 int32_t n_groups, bf_precision prec, const void *R, bool device_ptrs) {
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
     if (n_groups < 0) return bf_fail(plan, BF_EINVAL, "negative n_groups");
-    if (prec < BF_FP32 || prec > BF_BF16X3) return bf_fail(plan, BF_EINVAL, "unknown precision %d", (int)prec);
-    if (scale && prec == BF_FP32) return bf_fail(plan, BF_EINVAL, "BF_FP32 takes complex64 S (scale_dev must be NULL)");
+    if (prec < BF_FP32 || prec >= N_PREC) return bf_fail(plan, BF_EINVAL, "unknown precision %d", (int)prec);
+    if (scale && simt_form(prec))
+        return bf_fail(plan, BF_EINVAL, "the FP32 forms take complex64 S (scale_dev must be NULL)");
     if (n_groups == 0) return BF_OK;
     if (!groups || !S || !R) return bf_fail(plan, BF_EINVAL, "NULL argument");
     if (device_ptrs && (!aligned16(S) || !aligned16(R)))
@@ -539,12 +540,12 @@ static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_byte
 }
 
 int max_cta_for(bf_plan plan, bf_precision prec) {
-    const int per_sm = prec == BF_FP32 ? std::max(1, std::min(plan->tune.simt_ctas_per_sm, plan->simt_resident)) : 1;
+    const int per_sm = simt_form(prec) ? std::max(1, std::min(plan->tune.simt_ctas_per_sm, plan->simt_resident)) : 1;
     return plan->sm_count * per_sm;
 }
 
 cudaError_t launch_kernel(bf_precision prec, bool held, const KParams &p, int n_cta, cudaStream_t st) {
-    if (prec == BF_FP32) return launch_simt(p, n_cta, st);
+    if (simt_form(prec)) return launch_simt(p, n_cta, st, prec == BF_FP32_3M);
     return launch_tc((int)prec, held, p, n_cta, st);
 }
 

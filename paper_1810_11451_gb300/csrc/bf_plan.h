@@ -22,21 +22,22 @@ __host__ __device__ constexpr int f_bucket(int f) {
 }
 
 struct TuneTable {
-    double ns_per_block[4][TUNE_BUCKETS];
-    int tile_blocks[4][TUNE_BUCKETS];
-    bool tuned[4] = {false, false, false, false};
+    double ns_per_block[N_PREC][TUNE_BUCKETS];
+    int tile_blocks[N_PREC][TUNE_BUCKETS];
+    bool tuned[N_PREC] = {false, false, false, false, false};
     int simt_ctas_per_sm = 2;  // set to the resident maximum when a plan is created
     TuneTable() {
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < N_PREC; ++p)
             for (int b = 0; b < TUNE_BUCKETS; ++b) {
                 ns_per_block[p][b] = 0.0;
                 tile_blocks[p][b] = 2;
             }
     }
-    int tile_blocks_for(int prec, int f) const { return tile_blocks[prec & 3][f_bucket(f)]; }
+    static int row(int prec) { return prec >= 0 && prec < N_PREC ? prec : 0; }
+    int tile_blocks_for(int prec, int f) const { return tile_blocks[row(prec)][f_bucket(f)]; }
     // Scheduling cost of n blocks at f whose S and R take `bytes_per_block`.
     double cost(int prec, int f, int n, double bytes_per_block) const {
-        return tuned[prec & 3] ? n * ns_per_block[prec & 3][f_bucket(f)] : n * bytes_per_block;
+        return tuned[row(prec)] ? n * ns_per_block[row(prec)][f_bucket(f)] : n * bytes_per_block;
     }
 };
 
@@ -75,7 +76,7 @@ struct WorkBuf {
 
 struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
-    int simt_resident = 2;  // CTAs of the CUDA-core kernel that fit on one SM
+    int simt_resident = 2;  // CTAs of the CUDA-core kernels that fit on one SM (the smaller of the two)
     std::string err;
     // precoder store (slots)
     int cap = 0;

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) bf_precoder_kernel(const float2 *__restri
         const float2 v = w[e];
         simt[k * N_ANT + i] = v.x;
         simt[n + k * N_ANT + i] = v.y;
+        simt[2 * n + k * N_ANT + i] = v.x + v.y;
     }
     const int kpad = kpad_of(f);
     uint8_t *hi = w_bf16x2 + (int64_t)jb.slot * W_BF16X2_STRIDE;

@@ -29,7 +29,7 @@ cudaError_t launch_errnorm(const float2 *R, const double2 *Rref, int64_t n_block
                            double *total, int grid, cudaStream_t st);
 
 struct KParams;
-cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream);
+cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream, bool three_products);
 cudaError_t launch_tc(int prec, bool held, const KParams &p, int n_cta, cudaStream_t stream);
 int simt_smem_bytes();
 int simt_resident_ctas();

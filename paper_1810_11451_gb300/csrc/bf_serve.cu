@@ -308,7 +308,7 @@ extern "C" bf_status bf_serve_set_precoders(bf_server srv, const void *W_dev, co
 extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticket) {
     if (!srv || !job || !ticket) return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "NULL argument");
     if (job->n_groups < 0 || (job->n_groups && !job->groups)) return bf_fail(srv->plan, BF_EINVAL, "bad groups");
-    if (job->prec < BF_FP32 || job->prec > BF_BF16X3) return bf_fail(srv->plan, BF_EINVAL, "bad precision");
+    if (job->prec < BF_FP32 || job->prec >= N_PREC) return bf_fail(srv->plan, BF_EINVAL, "bad precision");
     if (job->n_groups && (!job->S_dev || !job->R_dev || ((uintptr_t)job->S_dev & 15) || ((uintptr_t)job->R_dev & 15)))
         return bf_fail(srv->plan, BF_EINVAL, "S_dev and R_dev must be non-NULL and 16-byte aligned");
     JobRec rec;

@@ -53,14 +53,29 @@ constexpr int SIMT_MIN_CTAS = SIMT_RPW == 8 ? 2 : 3;   // resident CTAs per SM t
 constexpr int SIMT_NS = BF_SIMT_NS;                    // S ring stages
 constexpr int SIMT_NW = 2;                             // W buffers
 constexpr int SIMT_S_STAGE = F_LIMIT * S_BYTES_PER_F;  // 17,280 B
-constexpr int SIMT_OFF_S = SIMT_NW * SIMT_IMG_MAX;
-constexpr int SIMT_OFF_BAR = SIMT_OFF_S + SIMT_NS * SIMT_S_STAGE;
 constexpr int SIMT_NBARS = 2 * SIMT_NS + 2 * SIMT_NW;
-constexpr int SIMT_SMEM = SIMT_OFF_BAR + SIMT_NBARS * 8 + 16;
+// Shared-memory layout: W buffers (2 planes, or 3 for the three-product
+// form) | S ring | barriers.
+template <bool G3M>
+struct SimtCfg {
+    static constexpr int W_BUF = G3M ? SIMT3_IMG_MAX : SIMT_IMG_MAX;
+    static constexpr int OFF_S = SIMT_NW * W_BUF;
+    static constexpr int OFF_BAR = OFF_S + SIMT_NS * SIMT_S_STAGE;
+    static constexpr int SMEM = OFF_BAR + SIMT_NBARS * 8 + 16;
+};
 
+// G3M: the three-product form (BF_FP32_3M). Per antenna and resource element
+// it keeps P1 = sum Wr Sr, P2 = sum Wi Si and P3 = sum (Wr + Wi)(Sr + Si), 3
+// FFMA per complex multiply-add instead of 4, and writes Re = P1 - P2,
+// Im = (P3 - P1) - P2. Wr + Wi comes from the image's third plane (loading it
+// measured faster than adding the two planes in registers: 93.6 vs 98.3 us
+// on the full band); the form is still slower than the plain one (87.9 us):
+// this kernel is not bound by its FFMA count.
+template <bool G3M>
 __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KParams p) {
+    using C = SimtCfg<G3M>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SIMT_OFF_BAR);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + SIMT_NBARS);
     const uint32_t bar0 = bfd::smem_u32(bars);
     auto s_full = [&](int s) { return bar0 + 8u * s; };
@@ -107,9 +122,9 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                         ok = false;
                         break;
                     }
-                    const uint32_t bytes = (uint32_t)simt_img_bytes(tl.f);
+                    const uint32_t bytes = (uint32_t)simt_img_bytes(tl.f, G3M ? 3 : 2);
                     bfd::mbar_arrive_expect_tx(w_full(wb), bytes);
-                    bfd::bulk_g2s(bfd::smem_u32(smem + wb * SIMT_IMG_MAX),
+                    bfd::bulk_g2s(bfd::smem_u32(smem + wb * C::W_BUF),
                                   p.w_simt + (int64_t)tl.prec * W_SIMT_STRIDE, bytes, w_full(wb));
                     ++nW;
                 }
@@ -125,7 +140,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                         break;
                     }
                     bfd::mbar_arrive_expect_tx(s_full(st), bytes);
-                    bfd::bulk_g2s(bfd::smem_u32(smem + SIMT_OFF_S + st * SIMT_S_STAGE),
+                    bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_S + st * SIMT_S_STAGE),
                                   p.S + tl.s_off + (int64_t)b * bytes, bytes, s_full(st));
                     ++nS;
                 }
@@ -167,18 +182,55 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                 }
                 ++nW;
             }
-            const float *Wr = reinterpret_cast<const float *>(smem + wb * SIMT_IMG_MAX);
+            const float *Wr = reinterpret_cast<const float *>(smem + wb * C::W_BUF);
             const float *Wi = Wr + f * N_ANT;
+            const float *Ws = Wi + f * N_ANT;  // Wr + Wi (three-product form)
             for (int b = 0; b < tl.nblk; ++b) {
                 const int st = nS % SIMT_NS;
                 if (!bfd::mbar_wait(s_full(st), (nS / SIMT_NS) & 1, abort_flag, p.status)) {
                     ok = false;
                     break;
                 }
-                const float *Sb = reinterpret_cast<const float *>(smem + SIMT_OFF_S + st * SIMT_S_STAGE);
+                const float *Sb = reinterpret_cast<const float *>(smem + C::OFF_S + st * SIMT_S_STAGE);
                 float ar[SIMT_RPW][2], ai[SIMT_RPW][2];
 #pragma unroll
                 for (int r = 0; r < SIMT_RPW; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
+                if constexpr (G3M) {
+                    float p3[SIMT_RPW][2];  // ar holds P1, ai holds P2
+#pragma unroll
+                    for (int r = 0; r < SIMT_RPW; ++r) p3[r][0] = p3[r][1] = 0.f;
+#pragma unroll 2
+                    for (int k = 0; k < f; ++k) {
+                        const float4 s = *reinterpret_cast<const float4 *>(Sb + k * (2 * B_RE) + 4 * jl);
+                        const float s0 = s.x + s.y, s1 = s.z + s.w;
+#pragma unroll
+                        for (int q = 0; q < SIMT_RPW / 4; ++q) {
+                            const float4 w = *reinterpret_cast<const float4 *>(Wr + k * N_ANT + i0 + 4 * q);
+                            const float4 v = *reinterpret_cast<const float4 *>(Wi + k * N_ANT + i0 + 4 * q);
+                            const float4 u = *reinterpret_cast<const float4 *>(Ws + k * N_ANT + i0 + 4 * q);
+                            const float wr4[4] = {w.x, w.y, w.z, w.w}, wi4[4] = {v.x, v.y, v.z, v.w},
+                                        ws4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int r = 4 * q + e;
+                                ar[r][0] = fmaf(wr4[e], s.x, ar[r][0]);
+                                ai[r][0] = fmaf(wi4[e], s.y, ai[r][0]);
+                                p3[r][0] = fmaf(ws4[e], s0, p3[r][0]);
+                                ar[r][1] = fmaf(wr4[e], s.z, ar[r][1]);
+                                ai[r][1] = fmaf(wi4[e], s.w, ai[r][1]);
+                                p3[r][1] = fmaf(ws4[e], s1, p3[r][1]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < SIMT_RPW; ++r)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const float p1 = ar[r][c], p2 = ai[r][c];
+                            ar[r][c] = p1 - p2;
+                            ai[r][c] = (p3[r][c] - p1) - p2;
+                        }
+                } else {
 #pragma unroll 2
                 for (int k = 0; k < f; ++k) {
                     const float4 s = *reinterpret_cast<const float4 *>(Sb + k * (2 * B_RE) + 4 * jl);
@@ -201,6 +253,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                         ai[r][1] = fmaf(wr[r], s.w, ai[r][1]);
                         ai[r][1] = fmaf(wi[r], s.z, ai[r][1]);
                     }
+                }
                 }
                 __syncwarp();
                 if (lane == 0) bfd::mbar_arrive(s_empty(st));
@@ -225,33 +278,43 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
 // Raise the kernel's dynamic shared-memory limit (once per process, before
 // any launch or graph capture).
 cudaError_t configure_simt() {
-    return cudaFuncSetAttribute(bf_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SIMT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(bf_simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SimtCfg<false>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(bf_simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SimtCfg<true>::SMEM);
 }
 
-cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream) {
+cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream, bool g3m) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_cta);
     cfg.blockDim = dim3(SIMT_THREADS);
-    cfg.dynamicSmemBytes = SIMT_SMEM;
+    cfg.dynamicSmemBytes = g3m ? SimtCfg<true>::SMEM : SimtCfg<false>::SMEM;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see grid_dep_wait
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, bf_simt_kernel, p);
+    return g3m ? cudaLaunchKernelEx(&cfg, bf_simt_kernel<true>, p) : cudaLaunchKernelEx(&cfg, bf_simt_kernel<false>, p);
 }
 
-int simt_smem_bytes() { return SIMT_SMEM; }
+int simt_smem_bytes() { return SimtCfg<true>::SMEM; }
 
 // CTAs of the CUDA-core kernel that fit on one SM at once (registers, shared
 // memory, threads); a launch never asks for more than this many per SM.
+// The smaller resident count of the two CUDA-core kernels (they share one
+// CTAs-per-SM setting).
 int simt_resident_ctas() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bf_simt_kernel, SIMT_THREADS, SIMT_SMEM) != cudaSuccess) {
+    int n0 = 0, n1 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, bf_simt_kernel<false>, SIMT_THREADS,
+                                                      SimtCfg<false>::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, bf_simt_kernel<true>, SIMT_THREADS,
+                                                      SimtCfg<true>::SMEM) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
+    const int n = n0 < n1 ? n0 : n1;
     return n > 0 ? n : 1;
 }
 

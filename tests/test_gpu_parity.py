@@ -26,7 +26,7 @@ TOL_SPLIT = 1e-5
 TOL_SINGLE = 2e-2
 FORMS = [("fp32", bf.BF_FP32, False), ("bf16x3", bf.BF_BF16X3, False), ("bf16x3_held", bf.BF_BF16X3, True),
          ("bf16", bf.BF_BF16, False), ("bf16_held", bf.BF_BF16, True), ("fp16", bf.BF_FP16, False),
-         ("fp16_held", bf.BF_FP16, True)]
+         ("fp16_held", bf.BF_FP16, True), ("fp32_3m", bf.BF_FP32_3M, False)]
 
 
 @pytest.fixture(scope="module")
@@ -44,8 +44,12 @@ def _ref(batch):
     return oracle.apply_batch(batch.rounded(np.complex64))
 
 
+# forms checked against the oracle of the complex64-rounded inputs (per-block errors too)
+ACCURATE = (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3)
+
+
 def _tol(prec):
-    return {bf.BF_FP32: TOL_FP32, bf.BF_BF16X3: TOL_SPLIT}.get(prec, TOL_SINGLE)
+    return {bf.BF_FP32: TOL_FP32, bf.BF_FP32_3M: TOL_FP32, bf.BF_BF16X3: TOL_SPLIT}.get(prec, TOL_SINGLE)
 
 
 def _assert_close(R, ref, tol, what):
@@ -70,7 +74,7 @@ def test_small_config(plan, name, prec, held):
     """One 64x8 precoder, 16-QAM blocks (the small FP32 workload, 300 blocks)."""
     batch = wl.config_small(seed=0, n_blocks=300)
     R = run(plan, batch, prec, torch, held=held)
-    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
     _assert_close(R, ref, _tol(prec), name)
 
 
@@ -79,22 +83,22 @@ def test_fullband_scaled(plan, name, prec, held):
     """f = 36, 13 resource blocks x 14 symbols (odd tile counts per CTA run)."""
     batch = wl.config_fullband(seed=2, n_rb=13, n_sym=14)
     R = run(plan, batch, prec, torch, held=held)
-    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
     e = _assert_close(R, ref, _tol(prec), name)
-    if prec in (bf.BF_FP32, bf.BF_BF16X3):
+    if prec in ACCURATE:
         for g, (a, r) in enumerate(zip(R, ref)):
             num, den = oracle.errnorm_blocks(a, r)
             assert np.all(np.sqrt(num / den) <= _tol(prec)), f"{name}: group {g} per-block error"
     print(f"{name}: rel err {e:.3e}")
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[2], FORMS[4]],
-                         ids=["fp32", "bf16x3", "bf16x3_held", "bf16_held"])
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[2], FORMS[4], FORMS[7]],
+                         ids=["fp32", "bf16x3", "bf16x3_held", "bf16_held", "fp32_3m"])
 def test_uneven_scaled(plan, name, prec, held):
     """Uneven f (0..36) per group, geometric group sizes, mixed QAM orders."""
     batch = wl.config_uneven(seed=3, n_blocks=700)
     R = run(plan, batch, prec, torch, held=held)
-    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
     for a, f in zip(R, batch.f_of_group):
         if f == 0:
             assert np.all(a == 0)
@@ -159,14 +163,14 @@ def test_reduced_accuracy(plan):
     errs = {}
     for name, prec, held in FORMS[1:]:
         R = run(plan, batch, prec, torch, held=held)
-        errs[name] = _assert_close(R, ref32 if prec == bf.BF_BF16X3 else ref64, _tol(prec), name)
+        errs[name] = _assert_close(R, ref32 if prec in ACCURATE else ref64, _tol(prec), name)
     print("reduced-precision errors:", {k: f"{v:.2e}" for k, v in errs.items()})
 
 
 def test_graph_and_host_paths_bitwise(plan):
     """The graph-captured batch and the host-buffer pipeline give the same bits."""
     batch = wl.config_uneven(seed=9, n_blocks=400)
-    for prec in (bf.BF_FP32, bf.BF_BF16X3):
+    for prec in ACCURATE:
         a = run(plan, batch, prec, torch, mode="apply")
         others = [run(plan, batch, prec, torch, mode=m, set_w=False) for m in ("batch", "graph", "host", "apply")]
         for o in others:
@@ -179,7 +183,7 @@ def test_fullband_full_size(plan):
     the launch configuration the bench times, checked in full against the oracle."""
     batch = wl.config_fullband()
     ref = _ref(batch)
-    for prec in (bf.BF_FP32, bf.BF_BF16X3):
+    for prec in ACCURATE:
         R = run(plan, batch, prec, torch, mode="batch")
         e = _assert_close(R, ref, _tol(prec), f"fullband prec {prec}")
         print(f"full band prec {prec}: rel err {e:.3e}")
@@ -218,8 +222,12 @@ def test_edge_cases_and_errors(plan):
     with pytest.raises(bf.BfError) as ei:
         bf.bf_apply_batch(plan, S_t.data_ptr() + 4, None, [(100, 1, 0, 0)], bf.BF_FP32, R_t)
     assert ei.value.status == bf.BF_EINVAL
+    for prec in (bf.BF_FP32, bf.BF_FP32_3M):
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_apply_batch(plan, S_t, R_t, [(100, 1, 0, 0)], prec, R_t)  # the FP32 forms take no scale
+        assert ei.value.status == bf.BF_EINVAL
     with pytest.raises(bf.BfError) as ei:
-        bf.bf_apply_batch(plan, S_t, R_t, [(100, 1, 0, 0)], bf.BF_FP32, R_t)  # FP32 takes no scale
+        bf.bf_apply_batch(plan, S_t, None, [(100, 1, 0, 0)], 5, R_t)  # unknown precision
     assert ei.value.status == bf.BF_EINVAL
     with pytest.raises(bf.BfError) as ei:
         bf.bf_set_precoders(plan, S_t, [37], 0)  # f > f_max
@@ -265,13 +273,14 @@ def test_autotune_keeps_results_and_round_trips(plan, tmp_path):
         bf.bf_plan_destroy(other)
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4]], ids=["fp32", "bf16x3", "bf16_held"])
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4], FORMS[7]],
+                         ids=["fp32", "bf16x3", "bf16_held", "fp32_3m"])
 def test_uneven_full_size(plan, name, prec, held):
     """The uneven workload at full size (16,384 blocks) in one persistent launch,
     checked in full against the oracle."""
     batch = wl.config_uneven()
     R = run(plan, batch, prec, torch, held=held, mode="batch")
-    ref = _ref(batch) if prec in (bf.BF_FP32, bf.BF_BF16X3) else oracle.apply_batch(batch)
+    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
     e = _assert_close(R, ref, _tol(prec), name)
     print(f"uneven full size {name}: {e:.3e}")
 
