@@ -289,7 +289,11 @@ def uneven_leg(torch, bf, plan, batch, ref_d, stream, steps=200):
             t0 = time.perf_counter()
             bf.bf_autotune(plan, bf.BF_BF16X3, stream)
             bf.bf_autotune(plan, bf.BF_FP32, stream)
+            bf.bf_autotune(plan, bf.BF_FP32_3M, stream)
             out["autotune_s"] = time.perf_counter() - t0
+            names = {v: k for k, v in bf.PRECISIONS.items()}
+            form, ns = bf.bf_select_form(plan, bf.BF_TARGET_FP32, lay.groups)
+            out["selected_form_fp32_target"] = {"form": names[form], "predicted_marginal_us": ns / 1e3}
             out["tune_table"] = {name: [bf.bf_tune_query(plan, p, f) for f in (0, 8, 16, 24, 36)]
                                  for name, p in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32))}
         for name, prec in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32)):

@@ -288,6 +288,24 @@ bf_status bf_tune_query(bf_plan plan, bf_precision prec, int32_t f, double *ns_p
 bf_status bf_tune_save(bf_plan plan, const char *path);
 bf_status bf_tune_load(bf_plan plan, const char *path);
 
+/* Accuracy targets of bf_select_form, from the accuracy classes of the
+ * reduced-precision study: BF_TARGET_FP32 (relative Frobenius error <= 1e-5)
+ * is met by BF_FP32, BF_FP32_3M and BF_BF16X3; BF_TARGET_BF16 (<= 2e-2) by
+ * every form. */
+typedef enum { BF_TARGET_FP32 = 0, BF_TARGET_BF16 = 1 } bf_target;
+
+/* The optimizer's building-block choice for one batch (Sec. IV: the best
+ * block per size and target). Among the forms that meet `target` and are
+ * tuned on this plan (bf_autotune or bf_tune_load), returns in *prec_out the
+ * one with the smallest predicted time for these groups: the sum over groups
+ * of n_blocks times the measured marginal ns per block of the group's f
+ * bucket, for complex64 S. *ns_out (may be NULL) receives that prediction.
+ * With no tuned candidate it returns the default form (BF_BF16X3 for
+ * BF_TARGET_FP32, BF_BF16 for BF_TARGET_BF16) and *ns_out = 0. Host only: no
+ * CUDA call. Groups must name set precoder slots (BF_ENOTFOUND otherwise). */
+bf_status bf_select_form(bf_plan plan, bf_target target, const bf_group *groups, int32_t n_groups,
+                         bf_precision *prec_out, double *ns_out);
+
 /* ------------------------------------------------------------------ accuracy report */
 
 /* Relative Frobenius error of R against a reference, accumulated in FP64.

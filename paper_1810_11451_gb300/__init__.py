@@ -361,6 +361,20 @@ def bf_autotune(plan, prec: int, stream=None) -> None:
     _check(_tune_sigs(lib()).bf_autotune(plan, int(prec), _stream(stream)), plan)
 
 
+BF_TARGET_FP32, BF_TARGET_BF16 = 0, 1
+
+
+def bf_select_form(plan, target: int, groups) -> Tuple[int, float]:
+    """(form, predicted marginal ns) chosen from the tuned table for these groups."""
+    L = lib()
+    L.bf_select_form.restype = c_int
+    L.bf_select_form.argtypes = [c_void_p, c_int, POINTER(bf_group), c_int32, POINTER(c_int), POINTER(c_double)]
+    ga, n = make_groups(groups)
+    p, ns = c_int(), c_double()
+    _check(L.bf_select_form(plan, int(target), ga, n, ctypes.byref(p), ctypes.byref(ns)), plan)
+    return p.value, ns.value
+
+
 def bf_tune_query(plan, prec: int, f: int) -> dict:
     ns, tb, tuned = c_double(), c_int32(), c_int32()
     _check(_tune_sigs(lib()).bf_tune_query(plan, int(prec), int(f), ctypes.byref(ns), ctypes.byref(tb),

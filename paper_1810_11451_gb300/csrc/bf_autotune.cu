@@ -226,3 +226,35 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
     plan->tune = T;
     return BF_OK;
 }
+
+extern "C" bf_status bf_select_form(bf_plan plan, bf_target target, const bf_group *groups, int32_t n_groups,
+                                    bf_precision *prec_out, double *ns_out) {
+    if (!plan || !prec_out || n_groups < 0 || (n_groups > 0 && !groups) ||
+        (target != BF_TARGET_FP32 && target != BF_TARGET_BF16))
+        return bf_fail(plan, BF_EINVAL, "bad arguments");
+    for (int g = 0; g < n_groups; ++g)
+        if (groups[g].n_blocks < 0 || groups[g].prec_id < 0 || groups[g].prec_id >= plan->cap ||
+            plan->f_slot[groups[g].prec_id] < 0)
+            return bf_fail(plan, BF_ENOTFOUND, "group %d: precoder slot %d is not set", g, groups[g].prec_id);
+    static const bf_precision fp32_forms[] = {BF_BF16X3, BF_FP32, BF_FP32_3M};
+    static const bf_precision all_forms[] = {BF_BF16, BF_FP16, BF_BF16X3, BF_FP32, BF_FP32_3M};
+    const bf_precision *cand = target == BF_TARGET_FP32 ? fp32_forms : all_forms;
+    const int n_cand = target == BF_TARGET_FP32 ? 3 : 5;
+    const TuneTable &T = plan->tune;
+    bf_precision best = cand[0];
+    double best_ns = -1.0;
+    for (int i = 0; i < n_cand; ++i) {
+        const int p = (int)cand[i];
+        if (!T.tuned[p]) continue;
+        double ns = 0.0;
+        for (int g = 0; g < n_groups; ++g)
+            ns += (double)groups[g].n_blocks * T.ns_per_block[p][f_bucket(plan->f_slot[groups[g].prec_id])];
+        if (best_ns < 0 || ns < best_ns) {
+            best_ns = ns;
+            best = cand[i];
+        }
+    }
+    *prec_out = best;
+    if (ns_out) *ns_out = best_ns < 0 ? 0.0 : best_ns;
+    return BF_OK;
+}
