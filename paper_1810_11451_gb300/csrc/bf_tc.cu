@@ -51,7 +51,11 @@ static_assert(TC_CONV_WARPS % 4 == 0 && TC_EPI_WARPS % 4 == 0 && TC_EPI_WARPS <=
 constexpr int TC_CONV0 = 4;                          // first converter warp
 constexpr int TC_EPI0 = TC_CONV0 + TC_CONV_WARPS;    // first epilogue warp (a multiple of 4)
 constexpr int TC_THREADS = 32 * (TC_EPI0 + TC_EPI_WARPS);
-constexpr int TC_NACC = 4;       // accumulators in tensor memory
+#ifndef BF_TC_NACC
+#define BF_TC_NACC 4
+#endif
+constexpr int TC_NACC = BF_TC_NACC;  // accumulators in tensor memory (2 or 4: a power-of-two allocation)
+static_assert(TC_NACC == 2 || TC_NACC == 4, "tensor-memory allocation is a power of two columns");
 constexpr int TC_ACC_COLS = 128; // N
 constexpr int TC_RAW_SLOT = F_LIMIT * S_BYTES_PER_F;  // one complex64 block, 17,280 B
 constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shared memory per CTA
