@@ -166,8 +166,20 @@ def cpu_baseline(batch, budget_s: float = 12.0):
             break
     dt = time.perf_counter() - t0
     gflops = batch.flops() * reps / dt / 1e9
-    return {"value": gflops, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"the whole workload ({batch.total_blocks} blocks) x {reps} repetitions, {dt:.1f} s, FP64"}, ref
+    cores = oracle.num_threads()
+    # the same oracle on one core, over the first 20 resource blocks (280 blocks)
+    one = type(rb)(rb.W, rb.prec[:20], rb.S[:20], rb.name)
+    oracle.set_num_threads(1)
+    t1, reps1 = time.perf_counter(), 0
+    while time.perf_counter() - t1 < 2.0 or reps1 < 1:
+        oracle.apply_batch(one)
+        reps1 += 1
+    dt1 = time.perf_counter() - t1
+    oracle.set_num_threads(cores)
+    return {"value": gflops, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload ({batch.total_blocks} blocks) x {reps} repetitions, {dt:.1f} s, FP64",
+            "single_core": {"value": one.flops() * reps1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": f"first 20 resource blocks ({one.total_blocks} blocks) x {reps1}, {dt1:.1f} s"}}, ref
 
 
 def cpu_references(done, batches):

@@ -100,6 +100,12 @@ bf_status bf_wait(bf_server srv, uint64_t ticket, int64_t timeout_us, double *la
  * Used to model a stalled producer. */
 bf_status bf_serve_pause(bf_server srv, int32_t paused);
 
+/* Change the HBM admission budget (> 0, BF_EINVAL otherwise). Jobs in flight
+ * keep running; later admissions use the new budget, and a larger budget
+ * admits waiting jobs at once. BF_EBUSY (budget unchanged) if a queued job
+ * needs more than the new budget, since it could then never be admitted. */
+bf_status bf_serve_set_budget(bf_server srv, int64_t hbm_budget_bytes);
+
 bf_status bf_serve_get_stats(bf_server srv, bf_serve_stats *out);
 
 #ifdef __cplusplus

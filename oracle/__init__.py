@@ -65,6 +65,8 @@ def _bind(path: str):
     lib.bfo_dft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
     lib.bfo_dft.restype = None
     lib.bfo_num_threads.restype = ctypes.c_int
+    lib.bfo_set_num_threads.argtypes = [ctypes.c_int]
+    lib.bfo_set_num_threads.restype = None
     lib.bfo_mutant_id.restype = ctypes.c_int
     return lib
 
@@ -84,6 +86,11 @@ def load_variant(path: str):
 
 def num_threads() -> int:
     return int(lib().bfo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Run the oracle on n threads from now on (timing on one core)."""
+    lib().bfo_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------

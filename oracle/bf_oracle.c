@@ -96,6 +96,18 @@ void bfo_apply_blocks(int n_ant, int f, int b, long long n_blocks,
         bfo_block(n_ant, f, b, W, S + (size_t)n * s_stride, R + (size_t)n * r_stride);
 }
 
+/* Use n OpenMP threads from now on (no effect without OpenMP). */
+void bfo_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int bfo_num_threads(void)
 {

@@ -438,6 +438,7 @@ def _serve_sigs(L):
         ("bf_poll", c_int, [c_void_p, ctypes.c_uint64, POINTER(c_int), POINTER(c_double)]),
         ("bf_wait", c_int, [c_void_p, ctypes.c_uint64, c_int64, POINTER(c_double)]),
         ("bf_serve_pause", c_int, [c_void_p, c_int32]),
+        ("bf_serve_set_budget", c_int, [c_void_p, c_int64]),
         ("bf_serve_get_stats", c_int, [c_void_p, POINTER(bf_serve_stats)]),
     ]:
         fn = getattr(L, name)
@@ -504,6 +505,10 @@ def bf_wait(srv, ticket: int, timeout_us: int) -> float:
 
 def bf_serve_pause(srv, paused: bool) -> None:
     _serve_sigs(lib()).bf_serve_pause(srv, int(bool(paused)))
+
+
+def bf_serve_set_budget(srv, hbm_budget_bytes: int) -> None:
+    _check(_serve_sigs(lib()).bf_serve_set_budget(srv, int(hbm_budget_bytes)))
 
 
 def bf_serve_get_stats(srv) -> dict:

@@ -393,6 +393,21 @@ extern "C" bf_status bf_serve_pause(bf_server srv, int32_t paused) {
     return BF_OK;
 }
 
+extern "C" bf_status bf_serve_set_budget(bf_server srv, int64_t hbm_budget_bytes) {
+    if (!srv) return bf_fail(nullptr, BF_EINVAL, "server is NULL");
+    if (hbm_budget_bytes <= 0) return bf_fail(srv->plan, BF_EINVAL, "budget must be positive");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (uint64_t t : srv->queue) {
+        const auto it = srv->jobs.find(t);
+        if (it != srv->jobs.end() && it->second.bytes > hbm_budget_bytes)
+            return bf_fail(srv->plan, BF_EBUSY, "a queued job needs %lld bytes, more than %lld",
+                           (long long)it->second.bytes, (long long)hbm_budget_bytes);
+    }
+    srv->cfg.hbm_budget_bytes = hbm_budget_bytes;
+    srv->cv_work.notify_all();
+    return BF_OK;
+}
+
 extern "C" bf_status bf_serve_get_stats(bf_server srv, bf_serve_stats *out) {
     if (!srv || !out) return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(srv->mu);

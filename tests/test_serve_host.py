@@ -68,6 +68,28 @@ def test_budget_limits_inflight_bytes(bf):
         bf.bf_serve_destroy(srv)
 
 
+def test_budget_can_change_at_run_time(bf):
+    per_job = 3 * R_BLOCK
+    srv = bf.bf_serve_create(None, n_slots=4, max_batch_jobs=1, hbm_budget_bytes=per_job, fake_device_us=20000)
+    try:
+        bf.bf_serve_pause(srv, True)
+        ts = [bf.bf_submit(srv, job_groups(3), bf.BF_FP32, FAKE_S, FAKE_R) for _ in range(4)]
+        with pytest.raises(bf.BfError) as ei:  # a queued job could never be admitted
+            bf.bf_serve_set_budget(srv, per_job - 1)
+        assert ei.value.status == bf.BF_EBUSY
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_serve_set_budget(srv, 0)
+        assert ei.value.status == bf.BF_EINVAL
+        bf.bf_serve_set_budget(srv, 4 * per_job)  # room for all four at once
+        bf.bf_serve_pause(srv, False)
+        for t in ts:
+            bf.bf_wait(srv, t, 10_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["max_busy_slots"] == 4 and st["max_inflight_bytes"] == 4 * per_job
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
 def test_continuous_batching_merges_and_overlaps(bf):
     srv = bf.bf_serve_create(None, n_slots=2, max_batch_jobs=8, hbm_budget_bytes=1 << 34, fake_device_us=50000)
     try:
