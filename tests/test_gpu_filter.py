@@ -93,6 +93,16 @@ def test_closed_forms(filt):
         assert rel(y[i], np.roll(hp, n0)) <= TOL
 
 
+@pytest.mark.parametrize("n_taps", [1, 2, 2047, 2048])
+def test_tap_counts(filt, n_taps):
+    """Filter sequences from one tap to the full 2048, against the oracle."""
+    rng = np.random.default_rng(n_taps)
+    h = (rng.normal(size=n_taps) + 1j * rng.normal(size=n_taps)).astype(np.complex64)
+    s = (rng.normal(size=(6, N)) + 1j * rng.normal(size=(6, N))).astype(np.complex64)
+    y = run(filt, h, s)
+    assert np.all(np.isfinite(y)) and rel(y, oracle.circular_filter(h, s)) <= TOL
+
+
 @pytest.mark.parametrize("n_sig", [1, 3, 607, 1001, 2000])
 def test_ragged_counts(filt, n_sig):
     """Counts that leave teams idle, and counts above the number of resident

@@ -178,6 +178,37 @@ def test_graph_and_host_paths_bitwise(plan):
                 assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
 
 
+def test_host_path_scattered_buffers(plan):
+    """bf_apply_batch_host over several chunks with the groups stored in reverse
+    order and 16-byte gaps in both host buffers: every group equals the
+    device path bit for bit and the gaps keep their fill."""
+    batch = wl.config_uneven(seed=21, n_blocks=6000)
+    ref = run(plan, batch, bf.BF_BF16X3, torch)
+    G, nb, fs = batch.n_groups, batch.n_blocks, batch.f_of_group
+    s_offs, r_offs, so, ro = [0] * G, [0] * G, 16, 32
+    for g in reversed(range(G)):
+        s_offs[g], r_offs[g] = so, ro
+        so += nb[g] * fs[g] * 480 + 16
+        ro += nb[g] * 30720 + 16
+    S_h = torch.zeros(so // 4, dtype=torch.float32).pin_memory()
+    R_h = torch.full((ro // 4,), float("nan"), dtype=torch.float32).pin_memory()
+    s_np = S_h.numpy().view(np.uint8)
+    for g in range(G):
+        blk = np.ascontiguousarray(batch.S[g].astype(np.complex64)).view(np.uint8).ravel()
+        s_np[s_offs[g]:s_offs[g] + blk.size] = blk
+    groups = [(batch.prec[g], nb[g], s_offs[g], r_offs[g]) for g in range(G)]
+    bf.bf_apply_batch_host(plan, S_h, groups, bf.BF_BF16X3, R_h)
+    torch.cuda.synchronize()
+    r_np = R_h.numpy().view(np.uint8)
+    written = np.zeros(r_np.size, bool)
+    for g in range(G):
+        n = nb[g] * 30720
+        got = r_np[r_offs[g]:r_offs[g] + n].view(np.uint64)
+        assert np.array_equal(got, ref[g].view(np.uint64).ravel()), f"group {g}"
+        written[r_offs[g]:r_offs[g] + n] = True
+    assert np.all(np.isnan(R_h.numpy()[~written.reshape(-1, 4).all(axis=1)]))
+
+
 def test_fullband_full_size(plan):
     """The full-band f = 36 workload at full size (273 x 14 = 3,822 blocks) in
     the launch configuration the bench times, checked in full against the oracle."""
