@@ -493,6 +493,26 @@ def filter_leg(torch, bf, b, sample, stream, steps=100):
     return out
 
 
+def finite_json(obj):
+    """The JSON line with non-finite numbers (skipped legs) as null."""
+    if isinstance(obj, float):
+        return obj if np.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: finite_json(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [finite_json(v) for v in obj]
+    return obj
+
+
+def run_leg(legs, name, fn, *args):
+    """Run one secondary workload; a failure is reported in its entry and the
+    headline line is still printed."""
+    try:
+        legs[name] = fn(*args)
+    except Exception as e:  # reported, not hidden: the entry carries the error
+        legs[name] = {"error": f"{type(e).__name__}: {e}"}
+
+
 def serving_leg(torch, bf, ttis, prec):
     """Continuous-batching serving of 8 cells in real time (0.5 ms TTIs)."""
     import workloads as wl
@@ -609,22 +629,22 @@ def main():
     # ---- the other workloads: uneven batching, reduced precision, serving
     legs = {}
     if extra and "fused_output" in want:
-        legs["fused_output"] = fused_output_leg(torch, bf, plan, batch, ref_full, stream)
+        run_leg(legs, "fused_output", fused_output_leg, torch, bf, plan, batch, ref_full, stream)
     ref_full = None
     if b_uneven is not None:
         ref_d = to_device_ref(torch, refs.pop("uneven", None))
-        legs["uneven"] = uneven_leg(torch, bf, plan, b_uneven, ref_d, stream)
+        run_leg(legs, "uneven", uneven_leg, torch, bf, plan, b_uneven, ref_d, stream)
         del ref_d
     if b_reduced is not None:
         ref_d = to_device_ref(torch, refs.pop("reduced", None))
-        legs["reduced"] = reduced_leg(torch, bf, plan, b_reduced, ref_d, stream)
+        run_leg(legs, "reduced", reduced_leg, torch, bf, plan, b_reduced, ref_d, stream)
         del ref_d
         torch.cuda.empty_cache()
     if b_filter is not None:
-        legs["filter"] = filter_leg(torch, bf, b_filter, filter_sample, stream)
+        run_leg(legs, "filter", filter_leg, torch, bf, b_filter, filter_sample, stream)
     if extra and "serving" in want:
-        legs["serving_bf16x3"] = serving_leg(torch, bf, args.serving_ttis, bf.BF_BF16X3)
-        legs["serving_fp32"] = serving_leg(torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
+        run_leg(legs, "serving_bf16x3", serving_leg, torch, bf, args.serving_ttis, bf.BF_BF16X3)
+        run_leg(legs, "serving_fp32", serving_leg, torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
     status = bf.bf_device_status(plan)
 
     peak, peak_kind = peaks()
@@ -656,11 +676,11 @@ def main():
     }
     if legs:
         srv = legs.get("serving_bf16x3", {})
-        line["p99_tti_latency_ms"] = srv.get("p99_us", float("nan")) / 1e3 if srv else None
+        line["p99_tti_latency_ms"] = srv["p99_us"] / 1e3 if "p99_us" in srv else None
         line["legs"] = legs
     bf.bf_plan_destroy(plan)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(finite_json(line)), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
