@@ -12,7 +12,10 @@
 // antennas (rows of R); lane l owns resource elements 2l and 2l+1 (lanes 30
 // and 31 idle). Per flow k a lane reads its two S values with one 16-byte
 // shared load and the warp's 8+8 W values as broadcasts, then issues 64 FFMA.
-// R rows are written with 16-byte stores, 480 contiguous bytes per warp.
+// R rows are written with 16-byte stores, 480 contiguous bytes per warp
+// (8-byte stores for 16-bit R types; rows and blocks at the layout's strides).
+// The kernel is templated on the three-product form (BF_FP32_3M), which keeps
+// three sums per output element and reads a third precoder plane.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
