@@ -91,7 +91,8 @@ typedef struct bf_plan_s *bf_plan;
 bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out);
 
 /* Free the plan and everything it owns. Synchronises the device first.
- * NULL is accepted (BF_OK). */
+ * NULL is accepted (BF_OK). BF_EBUSY (nothing freed) while a serving engine
+ * created on the plan (bf_serve_create) has not been destroyed. */
 bf_status bf_plan_destroy(bf_plan plan);
 
 /* Human-readable text of the plan's last error ("" if none). Valid until the

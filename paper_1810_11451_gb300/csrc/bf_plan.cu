@@ -164,6 +164,8 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
 
 extern "C" bf_status bf_plan_destroy(bf_plan plan) {
     if (!plan) return BF_OK;
+    if (plan->servers.load() > 0)
+        return bf_fail(plan, BF_EBUSY, "%d serving engine(s) still use this plan", plan->servers.load());
     cudaSetDevice(plan->device);
     cudaDeviceSynchronize();
     cudaGetLastError();

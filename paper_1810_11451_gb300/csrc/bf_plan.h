@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -109,6 +110,7 @@ struct bf_plan_s {
     // tuning and counters
     bfi::TuneTable tune;
     int64_t launches = 0;
+    std::atomic<int> servers{0};  // serving engines attached to this plan
 };
 
 bf_status bf_fail(bf_plan plan, bf_status s, const char *fmt, ...);

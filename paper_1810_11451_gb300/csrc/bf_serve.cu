@@ -260,6 +260,7 @@ extern "C" bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, b
         }
     }
     s->th = std::thread(dispatcher, s);
+    if (plan) plan->servers++;
     *out = s;
     return BF_OK;
 }
@@ -288,6 +289,7 @@ extern "C" bf_status bf_serve_destroy(bf_server srv, int64_t timeout_us) {
         cudaEventDestroy(srv->prep_ev);
         cudaGetLastError();
     }
+    if (srv->plan) srv->plan->servers--;
     delete srv;
     return BF_OK;
 }

@@ -125,3 +125,16 @@ def test_budget_serialises_and_precoder_update_is_ordered(plan):
         assert ei.value.status == bf.BF_ENOTFOUND
     finally:
         bf.bf_serve_destroy(srv)
+
+
+def test_plan_outlives_its_servers():
+    """A plan cannot be destroyed while a serving engine uses it."""
+    p = bf.bf_plan_create(64, 36, 60)
+    srv = bf.bf_serve_create(p, n_slots=2)
+    try:
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_plan_destroy(p)
+        assert ei.value.status == bf.BF_EBUSY
+    finally:
+        bf.bf_serve_destroy(srv)
+    bf.bf_plan_destroy(p)
