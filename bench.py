@@ -462,10 +462,24 @@ def filter_leg(torch, bf, b, sample, stream, steps=100):
     torch.cuda.synchronize()
     launches = bf.bf_filter_launch_count(f) - n0
     ms = e0.elapsed_time(e1) / steps
+    # latency-style figures beside the throughput: one block alone (what the
+    # paper timed on one core) and one slot (64 antennas x 14 symbols), each
+    # launched back to back
+    small = {}
+    for name, n_sig in (("one_block", 1), ("one_slot", 896)):
+        for _ in range(5):
+            bf.bf_filter_apply(f, S, n_sig, Y, stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(200):
+            bf.bf_filter_apply(f, S, n_sig, Y, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        small[name + "_us"] = a0.elapsed_time(a1) / 200 * 1e3
     moved = b.algorithmic_bytes()
     out = {"blocks": b.n_sig, "n": b.n, "kernel_ms": ms, "blocks_per_s": b.n_sig / ms * 1e3,
            "us_per_block_amortised": ms * 1e3 / b.n_sig, "gflops_conventional": b.flops() / ms / 1e6,
-           "moved_bytes": moved, "moved_gbs": moved / ms / 1e6, "gpu_launches": int(launches),
+           "moved_bytes": moved, "moved_gbs": moved / ms / 1e6, "gpu_launches": int(launches), **small,
            "paper_context_us_per_filter": {"original": 27, "intel_fft_library": 19,
                                            "hardware": "Intel Haswell (E9000 blade), one filter"}}
     if sample is not None:
