@@ -302,13 +302,15 @@ def uneven_leg(torch, bf, plan, batch, ref_d, stream, steps=200):
             bf.bf_autotune(plan, bf.BF_BF16X3, stream)
             bf.bf_autotune(plan, bf.BF_FP32, stream)
             bf.bf_autotune(plan, bf.BF_FP32_3M, stream)
+            bf.bf_autotune(plan, bf.BF_TF32X3, stream)
             out["autotune_s"] = time.perf_counter() - t0
             names = {v: k for k, v in bf.PRECISIONS.items()}
             form, ns = bf.bf_select_form(plan, bf.BF_TARGET_FP32, lay.groups)
             out["selected_form_fp32_target"] = {"form": names[form], "predicted_marginal_us": ns / 1e3}
             out["tune_table"] = {name: [bf.bf_tune_query(plan, p, f) for f in (0, 8, 16, 24, 36)]
-                                 for name, p in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32))}
-        for name, prec in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32)):
+                                 for name, p in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32),
+                                                 ("tf32x3", bf.BF_TF32X3))}
+        for name, prec in (("bf16x3", bf.BF_BF16X3), ("fp32", bf.BF_FP32), ("tf32x3", bf.BF_TF32X3)):
             h = bf.bf_batch_create(plan, S, None, lay.groups, prec, R)
             ms = graph_rate(torch, bf, h, steps, stream)
             ms_graph = graph_rate(torch, bf, h, steps, stream, graph=True)
@@ -581,6 +583,8 @@ def main():
     plain = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_FP32, R_sets[s]) for s in range(n_sets)}
     plain3 = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_FP32_3M, R_sets[s])
               for s in range(n_sets)}
+    tf32 = {s: bf.bf_batch_create(plan, S_sets[s], None, lay.groups, bf.BF_TF32X3, R_sets[s])
+            for s in range(n_sets)}
     handles = [best[s] for s in range(n_sets)]
     flops = batch.flops()
     alg_bytes = batch.algorithmic_bytes()
@@ -601,11 +605,12 @@ def main():
 
     # ---- the plain FP32 form on the same GPU
     k2 = max(50, args.steps // 10)
-    p_ms = p3_ms = float("nan")
+    p_ms = p3_ms = t32_ms = float("nan")
     if not args.no_plain:
         p_total = time_launches(torch, bf, [plain[s] for s in range(n_sets)], k2, args.warmup, stream)
         p_ms = p_total / k2
         p3_ms = time_launches(torch, bf, [plain3[s] for s in range(n_sets)], k2, args.warmup, stream) / k2
+        t32_ms = time_launches(torch, bf, [tf32[s] for s in range(n_sets)], k2, args.warmup, stream) / k2
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -628,7 +633,7 @@ def main():
         ref_full = refs.pop("fullband")
         Rref_d = to_device_ref(torch, ref_full)
         acc = {}
-        for name, h in (("bf16x3", best[0]), ("fp32", plain[0]), ("fp32_3m", plain3[0])):
+        for name, h in (("bf16x3", best[0]), ("fp32", plain[0]), ("fp32_3m", plain3[0]), ("tf32x3", tf32[0])):
             bf.bf_batch_launch(h, stream)
             num, den = bf.bf_errnorm(plan, R_sets[0], Rref_d, lay.r_blocks, None, stream)
             acc[name] = float(np.sqrt(num / den))
@@ -637,6 +642,7 @@ def main():
         bf.bf_batch_destroy(best[s])
         bf.bf_batch_destroy(plain[s])
         bf.bf_batch_destroy(plain3[s])
+        bf.bf_batch_destroy(tf32[s])
     del S_sets, R_sets
     torch.cuda.empty_cache()
 
@@ -676,10 +682,13 @@ def main():
                        "blocks_per_s": world * batch.total_blocks / (p_ms * 1e-3)},
         "fp32_3m": {"value": world * flops / (p3_ms * 1e-3) / 1e9 if p3_ms == p3_ms else None, "unit": UNIT,
                     "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add"},
+        "tf32x3": {"value": world * flops / (t32_ms * 1e-3) / 1e9 if t32_ms == t32_ms else None, "unit": UNIT,
+                   "kernel_ms": t32_ms, "hbm_gbs": alg_bytes / (t32_ms * 1e-3) / 1e9 if t32_ms == t32_ms else None,
+                   "form": "split-tf32 (hi*hi + hi*lo + lo*hi) tcgen05 kind::tf32, FP32 accumulate"},
         "speedup_vs_fp32_plain": p_ms / ms_step if p_ms == p_ms else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_for("bf_tc.cu"),
-                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "bf_tc_kernel<3,false,true>",
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "bf_tc_kernel<3,false,OP_BF16>",
                      "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": e2e,
         "cpu_baseline": cpu,

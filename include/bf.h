@@ -61,10 +61,21 @@ typedef enum {
  *  BF_FP16   : single-pass tensor-core form, operands rounded to binary16.
  *  BF_BF16X3 : split form, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
  *              R = Wh*Sh + Wh*Sl + Wl*Sh on the tensor cores.
- * The tensor-core forms take S either as complex64 (converted on chip, no
- * per-block scale) or "held": pre-encoded by bf_quantize_symbols with one
+ *  BF_TF32X3 : the same split with TF32 terms (hi = tf32(x), lo = tf32(x - hi),
+ *              both rounded to nearest even; 10 fraction bits each): about
+ *              2^-21 relative error per product where BF_BF16X3 has 2^-16.
+ *              S complex64 only (no held form).
+ * The 16-bit tensor-core forms take S either as complex64 (converted on chip,
+ * no per-block scale) or "held": pre-encoded by bf_quantize_symbols with one
  * power-of-two scale per block. W is always taken from the plan's images. */
-typedef enum { BF_FP32 = 0, BF_BF16 = 1, BF_FP16 = 2, BF_BF16X3 = 3, BF_FP32_3M = 4 } bf_precision;
+typedef enum {
+    BF_FP32 = 0,
+    BF_BF16 = 1,
+    BF_FP16 = 2,
+    BF_BF16X3 = 3,
+    BF_FP32_3M = 4,
+    BF_TF32X3 = 5
+} bf_precision;
 
 /* One group: n_blocks consecutive blocks that all multiply precoder prec_id.
  * s_off / r_off are BYTE offsets of the group's first block in the S and R
@@ -291,8 +302,8 @@ bf_status bf_tune_load(bf_plan plan, const char *path);
 
 /* Accuracy targets of bf_select_form, from the accuracy classes of the
  * reduced-precision study: BF_TARGET_FP32 (relative Frobenius error <= 1e-5)
- * is met by BF_FP32, BF_FP32_3M and BF_BF16X3; BF_TARGET_BF16 (<= 2e-2) by
- * every form. */
+ * is met by BF_FP32, BF_FP32_3M, BF_BF16X3 and BF_TF32X3; BF_TARGET_BF16
+ * (<= 2e-2) by every form. */
 typedef enum { BF_TARGET_FP32 = 0, BF_TARGET_BF16 = 1 } bf_target;
 
 /* The optimizer's building-block choice for one batch (Sec. IV: the best

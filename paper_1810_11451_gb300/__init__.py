@@ -24,8 +24,9 @@ LIB_PATH = os.path.join(HERE, "libbf.so")
 BF_OK, BF_EINVAL, BF_ENOMEM, BF_EBUDGET, BF_ECUDA, BF_ETIMEOUT, BF_EAGAIN, BF_EBUSY, \
     BF_ENOTREADY, BF_ENOTFOUND = range(10)
 # bf_precision
-BF_FP32, BF_BF16, BF_FP16, BF_BF16X3, BF_FP32_3M = range(5)
-PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "fp16": BF_FP16, "bf16x3": BF_BF16X3, "fp32_3m": BF_FP32_3M}
+BF_FP32, BF_BF16, BF_FP16, BF_BF16X3, BF_FP32_3M, BF_TF32X3 = range(6)
+PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "fp16": BF_FP16, "bf16x3": BF_BF16X3, "fp32_3m": BF_FP32_3M,
+              "tf32x3": BF_TF32X3}
 
 N_ANT, B_RE, F_LIMIT = 64, 60, 36
 S_BYTES_PER_F = B_RE * 8      # one flow row of a complex64 S block

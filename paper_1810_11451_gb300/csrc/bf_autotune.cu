@@ -196,7 +196,7 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
         snprintf(key, sizeof key, "\"precision\": %d,", p);
         pos = txt.find(key);
         if (pos == std::string::npos) {
-            if (p == BF_FP32_3M) continue;  // tables written before that form existed
+            if (p >= BF_FP32_3M) continue;  // tables written before these forms existed
             return bad("missing precision");
         }
         int tuned = 0;
@@ -236,10 +236,10 @@ extern "C" bf_status bf_select_form(bf_plan plan, bf_target target, const bf_gro
         if (groups[g].n_blocks < 0 || groups[g].prec_id < 0 || groups[g].prec_id >= plan->cap ||
             plan->f_slot[groups[g].prec_id] < 0)
             return bf_fail(plan, BF_ENOTFOUND, "group %d: precoder slot %d is not set", g, groups[g].prec_id);
-    static const bf_precision fp32_forms[] = {BF_BF16X3, BF_FP32, BF_FP32_3M};
-    static const bf_precision all_forms[] = {BF_BF16, BF_FP16, BF_BF16X3, BF_FP32, BF_FP32_3M};
+    static const bf_precision fp32_forms[] = {BF_BF16X3, BF_TF32X3, BF_FP32, BF_FP32_3M};
+    static const bf_precision all_forms[] = {BF_BF16, BF_FP16, BF_BF16X3, BF_TF32X3, BF_FP32, BF_FP32_3M};
     const bf_precision *cand = target == BF_TARGET_FP32 ? fp32_forms : all_forms;
-    const int n_cand = target == BF_TARGET_FP32 ? 3 : 5;
+    const int n_cand = target == BF_TARGET_FP32 ? 4 : 6;
     const TuneTable &T = plan->tune;
     bf_precision best = cand[0];
     double best_ns = -1.0;

@@ -142,6 +142,12 @@ __host__ __device__ constexpr uint32_t idesc_f16(bool bf16, uint32_t M, uint32_t
            ((M >> 4) << 24);
 }
 
+// Instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator, A and B
+// both tf32 (format code 2 in both type fields), both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
 // D[tmem] (+)= A[smem] * B[smem]; accumulate when `acc` is non-zero.
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t acc) {
@@ -151,6 +157,25 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+// As umma_f16 with tf32 operands (K = 8 per instruction).
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// x rounded to the nearest TF32 value (10 fraction bits, ties to even), kept
+// as FP32 bits with the 13 low bits zero. Finite x; the carry out of the
+// fraction moves into the exponent, as rounding requires.
+__device__ __forceinline__ uint32_t tf32_rne_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
 }
 
 // Arrive (once) on an mbarrier when every tcgen05 operation this thread has

@@ -28,10 +28,20 @@ __host__ __device__ constexpr int64_t held_block_bytes(int f, int terms) {
     return (int64_t)terms * 64 * kpad_of(f) * 2;
 }
 
-// Precisions: the four tensor-core / CUDA-core forms and the three-product
-// CUDA-core form (BF_FP32_3M).
-constexpr int N_PREC = 5;
+// TF32 operands (BF_TF32X3): K = 2f rounded up to the MMA's K step of 8, and
+// 32-bit elements; same 128-row K-major image structure as the 16-bit kinds.
+__host__ __device__ constexpr int kpad32_of(int f) { return ((2 * f + 7) / 8) * 8; }
+__host__ __device__ constexpr int tf32_img_bytes(int kpad) { return 128 * kpad * 4; }
+constexpr int TF32_IMG_MAX = tf32_img_bytes(kpad32_of(F_LIMIT));  // 36,864
+
+// Precisions: the four tensor-core / CUDA-core forms, the three-product
+// CUDA-core form (BF_FP32_3M) and the TF32 split form (BF_TF32X3).
+constexpr int N_PREC = 6;
 __host__ __device__ constexpr bool simt_form(int prec) { return prec == BF_FP32 || prec == BF_FP32_3M; }
+// Forms that take held (pre-encoded 16-bit) S.
+__host__ __device__ constexpr bool held_form(int prec) {
+    return prec == BF_BF16 || prec == BF_FP16 || prec == BF_BF16X3;
+}
 
 // FP32 precoder image for the CUDA-core kernels: planar, flow-major,
 // Re W[i][k] at float index k*64 + i, Im W[i][k] at f*64 + k*64 + i, and
@@ -44,6 +54,7 @@ constexpr int SIMT3_IMG_MAX = simt_img_bytes(F_LIMIT, 3);  // 27,648
 constexpr int64_t W_SIMT_STRIDE = SIMT3_IMG_MAX;
 constexpr int64_t W_BF16X2_STRIDE = 2 * TC_IMG_MAX;  // hi image then lo image, compact
 constexpr int64_t W_FP16_STRIDE = TC_IMG_MAX;
+constexpr int64_t W_TF32X2_STRIDE = 2 * TF32_IMG_MAX;  // tf32 hi image then lo image, compact
 
 // One work item: up to two consecutive blocks of one group (same precoder).
 struct Tile {
@@ -69,7 +80,7 @@ struct KParams {
     uint8_t *R;
     const float *s_scale;      // per block (held S), else nullptr
     const uint8_t *w_simt;     // FP32 planar images, stride W_SIMT_STRIDE
-    const uint8_t *w_tc;       // bf16 hi|lo or fp16 images
+    const uint8_t *w_tc;       // bf16 hi|lo, fp16 or tf32 hi|lo images
     int64_t w_tc_stride;
     const float *w_scale;      // per slot: power of two undoing the image scale
     int *status;               // device status word

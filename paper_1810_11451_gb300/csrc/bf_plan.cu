@@ -174,8 +174,8 @@ extern "C" bf_status bf_plan_destroy(bf_plan plan) {
         if (w.h) cudaFreeHost(w.h);
         if (w.ev) cudaEventDestroy(w.ev);
     }
-    void *dev_ptrs[] = {plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_scale, plan->d_status,
-                        plan->prep_d, plan->en_d};
+    void *dev_ptrs[] = {plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_tf32x2, plan->w_scale,
+                        plan->d_status, plan->prep_d, plan->en_d};
     for (void *q : dev_ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < BF_XFER_SLOTS; ++i) {
@@ -214,16 +214,19 @@ extern "C" bf_status bf_device_status(bf_plan plan) {
 static bf_status ensure_slots(bf_plan plan, int need) {
     if (need <= plan->cap) return BF_OK;
     int ncap = std::max(need, std::max(64, plan->cap * 2));
-    uint8_t *ns = nullptr, *nb = nullptr, *nf = nullptr;
+    uint8_t *ns = nullptr, *nb = nullptr, *nf = nullptr, *nt = nullptr;
     float *nsc = nullptr;
     const size_t bs = (size_t)ncap * W_SIMT_STRIDE, bb = (size_t)ncap * W_BF16X2_STRIDE,
-                 bf = (size_t)ncap * W_FP16_STRIDE, bsc = (size_t)ncap * sizeof(float);
+                 bf = (size_t)ncap * W_FP16_STRIDE, bt = (size_t)ncap * W_TF32X2_STRIDE,
+                 bsc = (size_t)ncap * sizeof(float);
     if (cudaMalloc((void **)&ns, bs) != cudaSuccess || cudaMalloc((void **)&nb, bb) != cudaSuccess ||
-        cudaMalloc((void **)&nf, bf) != cudaSuccess || cudaMalloc((void **)&nsc, bsc) != cudaSuccess) {
+        cudaMalloc((void **)&nf, bf) != cudaSuccess || cudaMalloc((void **)&nt, bt) != cudaSuccess ||
+        cudaMalloc((void **)&nsc, bsc) != cudaSuccess) {
         cudaGetLastError();
         if (ns) cudaFree(ns);
         if (nb) cudaFree(nb);
         if (nf) cudaFree(nf);
+        if (nt) cudaFree(nt);
         if (nsc) cudaFree(nsc);
         return bf_fail(plan, BF_ENOMEM, "precoder store growth to %d slots failed", ncap);
     }
@@ -232,15 +235,18 @@ static bf_status ensure_slots(bf_plan plan, int need) {
         BF_CK(plan, cudaMemcpy(ns, plan->w_simt, (size_t)plan->cap * W_SIMT_STRIDE, cudaMemcpyDeviceToDevice));
         BF_CK(plan, cudaMemcpy(nb, plan->w_bf16x2, (size_t)plan->cap * W_BF16X2_STRIDE, cudaMemcpyDeviceToDevice));
         BF_CK(plan, cudaMemcpy(nf, plan->w_fp16, (size_t)plan->cap * W_FP16_STRIDE, cudaMemcpyDeviceToDevice));
+        BF_CK(plan, cudaMemcpy(nt, plan->w_tf32x2, (size_t)plan->cap * W_TF32X2_STRIDE, cudaMemcpyDeviceToDevice));
         BF_CK(plan, cudaMemcpy(nsc, plan->w_scale, (size_t)plan->cap * sizeof(float), cudaMemcpyDeviceToDevice));
         cudaFree(plan->w_simt);
         cudaFree(plan->w_bf16x2);
         cudaFree(plan->w_fp16);
+        cudaFree(plan->w_tf32x2);
         cudaFree(plan->w_scale);
     }
     plan->w_simt = ns;
     plan->w_bf16x2 = nb;
     plan->w_fp16 = nf;
+    plan->w_tf32x2 = nt;
     plan->w_scale = nsc;
     plan->f_slot.resize(ncap, -1);
     plan->cap = ncap;
@@ -278,7 +284,8 @@ extern "C" bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int
     }
     BF_CK(plan, cudaMemcpyAsync(plan->prep_d, plan->prep_h, bytes, cudaMemcpyHostToDevice, st));
     BF_CK(plan, launch_precoders(reinterpret_cast<const float2 *>(W_dev), reinterpret_cast<PrecJob *>(plan->prep_d),
-                                 n_prec, plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_scale, st));
+                                 n_prec, plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_tf32x2,
+                                 plan->w_scale, st));
     BF_CK(plan, cudaEventRecord(plan->prep_ev, st));
     for (int i = 0; i < n_prec; ++i) plan->f_slot[first_id + i] = f_host[i];
     return BF_OK;
@@ -463,7 +470,7 @@ extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const 
                                bf_precision prec, int32_t held, int32_t max_cta, bf_tile *tiles_out,
                                int32_t max_tiles, int32_t *cta_begin_out, int32_t *n_cta_out) {
     if (!f_of_slot || n_slots < 0 || n_groups < 0 || (n_groups && !groups) || max_cta < 1 || !n_cta_out ||
-        prec < BF_FP32 || prec >= N_PREC || (held && simt_form(prec)))
+        prec < BF_FP32 || prec >= N_PREC || (held && !held_form(prec)))
         return -BF_EINVAL;
     for (int g = 0; g < n_groups; ++g) {
         if (groups[g].prec_id < 0 || groups[g].prec_id >= n_slots || groups[g].n_blocks < 0) return -BF_EINVAL;
@@ -497,8 +504,8 @@ static bf_status validate_apply(bf_plan plan, const void *S, const float *scale,
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
     if (n_groups < 0) return bf_fail(plan, BF_EINVAL, "negative n_groups");
     if (prec < BF_FP32 || prec >= N_PREC) return bf_fail(plan, BF_EINVAL, "unknown precision %d", (int)prec);
-    if (scale && simt_form(prec))
-        return bf_fail(plan, BF_EINVAL, "the FP32 forms take complex64 S (scale_dev must be NULL)");
+    if (scale && !held_form(prec))
+        return bf_fail(plan, BF_EINVAL, "held S exists for BF_BF16, BF_FP16 and BF_BF16X3 only (scale_dev must be NULL)");
     if (n_groups == 0) return BF_OK;
     if (!groups || !S || !R) return bf_fail(plan, BF_EINVAL, "NULL argument");
     if (device_ptrs && (!aligned16(S) || !aligned16(R)))
@@ -530,8 +537,8 @@ static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_byte
     p.R = (uint8_t *)R;
     p.s_scale = scale;
     p.w_simt = plan->w_simt;
-    p.w_tc = prec == BF_FP16 ? plan->w_fp16 : plan->w_bf16x2;
-    p.w_tc_stride = prec == BF_FP16 ? W_FP16_STRIDE : W_BF16X2_STRIDE;
+    p.w_tc = prec == BF_FP16 ? plan->w_fp16 : prec == BF_TF32X3 ? plan->w_tf32x2 : plan->w_bf16x2;
+    p.w_tc_stride = prec == BF_FP16 ? W_FP16_STRIDE : prec == BF_TF32X3 ? W_TF32X2_STRIDE : W_BF16X2_STRIDE;
     p.w_scale = plan->w_scale;
     p.status = plan->d_status;
     p.r_row_stride = layout ? layout->row_stride : (int64_t)B_RE * 8;

@@ -25,7 +25,7 @@ __host__ __device__ constexpr int f_bucket(int f) {
 struct TuneTable {
     double ns_per_block[N_PREC][TUNE_BUCKETS];
     int tile_blocks[N_PREC][TUNE_BUCKETS];
-    bool tuned[N_PREC] = {false, false, false, false, false};
+    bool tuned[N_PREC] = {};
     int simt_ctas_per_sm = 2;  // set to the resident maximum when a plan is created
     TuneTable() {
         for (int p = 0; p < N_PREC; ++p)
@@ -82,7 +82,7 @@ struct bf_plan_s {
     // precoder store (slots)
     int cap = 0;
     std::vector<int> f_slot;  // -1 = unset
-    uint8_t *w_simt = nullptr, *w_bf16x2 = nullptr, *w_fp16 = nullptr;
+    uint8_t *w_simt = nullptr, *w_bf16x2 = nullptr, *w_fp16 = nullptr, *w_tf32x2 = nullptr;
     float *w_scale = nullptr;
     int *d_status = nullptr;
     // work-list ring

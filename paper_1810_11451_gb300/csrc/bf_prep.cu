@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "bf_device.cuh"
 #include "bf_internal.h"
 #include "bf_prep.h"
 
@@ -53,13 +54,20 @@ __device__ __forceinline__ int tc_offset(int row, int col, int kpad) {
     return (row >> 3) * (16 * kpad) + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2;
 }
 
+// The same for 32-bit (tf32) values: 8x4 tiles, 8-row groups 32*kpad bytes apart.
+__device__ __forceinline__ int tc_offset32(int row, int col, int kpad) {
+    return (row >> 3) * (32 * kpad) + (col >> 2) * 128 + (row & 7) * 16 + (col & 3) * 4;
+}
+
 // ------------------------------------------------------------------ precoders
 // One CTA per precoder. Writes the FP32 planar image, the bf16 hi|lo image,
-// the fp16 image (both scaled by 1/scale) and the scale.
+// the fp16 image, the tf32 hi|lo image (all three scaled by 1/scale) and the
+// scale.
 __global__ void __launch_bounds__(256) bf_precoder_kernel(const float2 *__restrict__ W,
                                                           const PrecJob *__restrict__ jobs,
                                                           uint8_t *w_simt, uint8_t *w_bf16x2,
-                                                          uint8_t *w_fp16, float *w_scale) {
+                                                          uint8_t *w_fp16, uint8_t *w_tf32x2,
+                                                          float *w_scale) {
     __shared__ float red[32];
     const PrecJob jb = jobs[blockIdx.x];
     const int f = jb.f, n = N_ANT * f;
@@ -82,10 +90,12 @@ __global__ void __launch_bounds__(256) bf_precoder_kernel(const float2 *__restri
         simt[n + k * N_ANT + i] = v.y;
         simt[2 * n + k * N_ANT + i] = v.x + v.y;
     }
-    const int kpad = kpad_of(f);
+    const int kpad = kpad_of(f), kpad32 = kpad32_of(f);  // kpad32 <= kpad
     uint8_t *hi = w_bf16x2 + (int64_t)jb.slot * W_BF16X2_STRIDE;
     uint8_t *lo = hi + tc_img_bytes(kpad);
     uint8_t *h16 = w_fp16 + (int64_t)jb.slot * W_FP16_STRIDE;
+    uint8_t *hi32 = w_tf32x2 + (int64_t)jb.slot * W_TF32X2_STRIDE;
+    uint8_t *lo32 = hi32 + tf32_img_bytes(kpad32);
     // B operand (N = 128 rows n = 2i + c, K = kpad columns kk = 2k + c'):
     // row 2i: (Re W, -Im W); row 2i+1: (Im W, Re W).
     for (int e = threadIdx.x; e < 128 * kpad; e += blockDim.x) {
@@ -104,14 +114,21 @@ __global__ void __launch_bounds__(256) bf_precoder_kernel(const float2 *__restri
         *reinterpret_cast<__nv_bfloat16 *>(hi + off) = bh;
         *reinterpret_cast<__nv_bfloat16 *>(lo + off) = bl;
         *reinterpret_cast<__half *>(h16 + off) = hh;
+        if (kk < kpad32) {
+            const uint32_t th = bfd::tf32_rne_bits(xs);
+            const int o32 = tc_offset32(nrow, kk, kpad32);
+            *reinterpret_cast<uint32_t *>(hi32 + o32) = th;
+            *reinterpret_cast<uint32_t *>(lo32 + o32) = bfd::tf32_rne_bits(xs - __uint_as_float(th));
+        }
     }
     if (threadIdx.x == 0) w_scale[jb.slot] = scale;
 }
 
 cudaError_t launch_precoders(const float2 *W, const PrecJob *jobs, int n_jobs, uint8_t *w_simt,
-                             uint8_t *w_bf16x2, uint8_t *w_fp16, float *w_scale, cudaStream_t st) {
+                             uint8_t *w_bf16x2, uint8_t *w_fp16, uint8_t *w_tf32x2, float *w_scale,
+                             cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
-    bf_precoder_kernel<<<n_jobs, 256, 0, st>>>(W, jobs, w_simt, w_bf16x2, w_fp16, w_scale);
+    bf_precoder_kernel<<<n_jobs, 256, 0, st>>>(W, jobs, w_simt, w_bf16x2, w_fp16, w_tf32x2, w_scale);
     return cudaGetLastError();
 }
 

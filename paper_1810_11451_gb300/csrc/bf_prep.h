@@ -22,7 +22,8 @@ struct QGroup {        // one group of S blocks to encode
 };
 
 cudaError_t launch_precoders(const float2 *W, const PrecJob *jobs, int n_jobs, uint8_t *w_simt,
-                             uint8_t *w_bf16x2, uint8_t *w_fp16, float *w_scale, cudaStream_t st);
+                             uint8_t *w_bf16x2, uint8_t *w_fp16, uint8_t *w_tf32x2, float *w_scale,
+                             cudaStream_t st);
 cudaError_t launch_quantize(int prec, const uint8_t *S, const QGroup *groups, int n_groups, int max_nb,
                             uint8_t *Sq, float *scale_out, cudaStream_t st);
 cudaError_t launch_errnorm(const float2 *R, const double2 *Rref, int64_t n_blocks, double *per_block,

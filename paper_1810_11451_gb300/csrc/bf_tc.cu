@@ -16,9 +16,13 @@
 //
 // Forms: TERMS = 1 is single pass (bf16 or fp16 operands); TERMS = 3 is the
 // split form Wh*Sh + Wh*Sl + Wl*Sh with x = hi + lo, hi = bf16(x), lo =
-// bf16(x - hi). HELD = false converts complex64 S on chip (raw ring ->
-// converter warps -> operand ring); HELD = true bulk-loads operand images
-// that bf_quantize_symbols encoded beforehand.
+// bf16(x - hi), or with tf32 terms (kind::tf32: 32-bit elements, K = 2f
+// padded to a multiple of 8, 8 per instruction). HELD = false converts
+// complex64 S on chip (raw ring -> converter warps -> operand ring); HELD =
+// true bulk-loads 16-bit operand images that bf_quantize_symbols encoded
+// beforehand. Every kind has the same image structure in bytes: K-major, no
+// swizzle, 8-row x 16-byte core matrices 128 bytes apart along K, 8-row
+// groups 8*kpad*esize bytes apart, and 32 bytes of K per instruction.
 //
 // Warp roles (384 threads, one CTA per SM):
 //   warp 0        bulk-loads S (raw complex64 or held images) into a ring
@@ -75,6 +79,11 @@ constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shar
 #ifndef BF_TC_SINGLE_HELD_STAGES
 #define BF_TC_SINGLE_HELD_STAGES 120
 #endif
+// tf32 split: one precoder buffer and one operand stage of 73,728 B each
+// leave room for four raw slots.
+#ifndef BF_TC_TF32_C64_STAGES
+#define BF_TC_TF32_C64_STAGES 114
+#endif
 struct Stages {
     int nw, na, nr;
 };
@@ -83,16 +92,31 @@ constexpr Stages STAGES[2][2] = {
     {decode_stages(BF_TC_SINGLE_C64_STAGES), decode_stages(BF_TC_SINGLE_HELD_STAGES)},
     {decode_stages(BF_TC_SPLIT_C64_STAGES), decode_stages(BF_TC_SPLIT_HELD_STAGES)}};
 
-template <int TERMS, bool HELD>
+// Operand kinds; the value is the format code of the instruction descriptor.
+constexpr int OP_FP16 = 0, OP_BF16 = 1, OP_TF32 = 2;
+
+template <int OPK>
+struct OpKind {
+    static constexpr int ES = OPK == OP_TF32 ? 4 : 2;  // bytes per element
+    static constexpr int KSTEP = 32 / ES;              // K of one instruction
+    __host__ __device__ static constexpr int kpad(int f) { return OPK == OP_TF32 ? kpad32_of(f) : kpad_of(f); }
+    __host__ __device__ static constexpr int img(int kp) { return OPK == OP_TF32 ? tf32_img_bytes(kp) : tc_img_bytes(kp); }
+    static constexpr int IMG_MAX = OPK == OP_TF32 ? TF32_IMG_MAX : TC_IMG_MAX;
+};
+
+template <int TERMS, bool HELD, int OPK>
 struct TcCfg {
+    static_assert(OPK != OP_TF32 || (TERMS == 3 && !HELD), "tf32 operands: split form on complex64 S only");
+    static constexpr int IMG = OpKind<OPK>::IMG_MAX;
     static constexpr int A_TERMS = TERMS == 3 ? 2 : 1;  // hi (and lo) operand images
     static constexpr int W_TERMS = TERMS == 3 ? 2 : 1;
-    static constexpr Stages ST = STAGES[TERMS == 3 ? 1 : 0][HELD ? 1 : 0];
+    static constexpr Stages ST =
+        OPK == OP_TF32 ? decode_stages(BF_TC_TF32_C64_STAGES) : STAGES[TERMS == 3 ? 1 : 0][HELD ? 1 : 0];
     static constexpr int NW = ST.nw;
     static constexpr int NA = ST.na;
     static constexpr int NR = HELD ? 0 : ST.nr;
-    static constexpr int W_BUF = W_TERMS * TC_IMG_MAX;
-    static constexpr int A_STAGE = A_TERMS * TC_IMG_MAX;
+    static constexpr int W_BUF = W_TERMS * IMG;
+    static constexpr int A_STAGE = A_TERMS * IMG;
     static constexpr int OFF_W = 0;
     static constexpr int OFF_A = OFF_W + NW * W_BUF;
     static constexpr int OFF_RAW = OFF_A + NA * A_STAGE;
@@ -124,9 +148,10 @@ __device__ __forceinline__ void store_r(uint8_t *dst, float re, float im, int r_
     else *reinterpret_cast<uint32_t *>(dst) = pack2_fp16(re, im);
 }
 
-template <int TERMS, bool HELD, bool BF16>
+template <int TERMS, bool HELD, int OPK>
 __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
-    using C = TcCfg<TERMS, HELD>;
+    using C = TcCfg<TERMS, HELD, OPK>;
+    using K = OpKind<OPK>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + C::NBARS);
@@ -145,7 +170,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     const uint32_t drain_bar = bar0 + 8u * (C::NBARS - 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr uint32_t IDESC = bfd::idesc_f16(BF16, 128, TC_ACC_COLS);
+    constexpr uint32_t IDESC =
+        OPK == OP_TF32 ? bfd::idesc_tf32(128, TC_ACC_COLS) : bfd::idesc_f16(OPK == OP_BF16, 128, TC_ACC_COLS);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::NR; ++s) {
@@ -240,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 if (tl.f == 0 || !(tl.flags & TF_FIRST_OF_W)) continue;
                 const int wb = n % C::NW;
                 if (!bfd::mbar_wait(w_empty(wb), ((n / C::NW) + 1) & 1, abort_flag, p.status)) break;
-                const uint32_t bytes = (uint32_t)(C::W_TERMS * tc_img_bytes(kpad_of(tl.f)));
+                const uint32_t bytes = (uint32_t)(C::W_TERMS * K::img(K::kpad(tl.f)));
                 bfd::mbar_arrive_expect_tx(w_full(wb), bytes);
                 bfd::bulk_g2s(bfd::smem_u32(smem + C::OFF_W + wb * C::W_BUF),
                               p.w_tc + (int64_t)tl.prec * p.w_tc_stride, bytes, w_full(wb));
@@ -265,22 +291,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 if (!bfd::mbar_wait(a_full(a), (n / C::NA) & 1, abort_flag, p.status)) break;
                 if (!bfd::mbar_wait(acc_empty(d), ((n / TC_NACC) + 1) & 1, abort_flag, p.status)) break;
                 bfd::tc_fence_after();
-                const int kp = kpad_of(tl.f);
-                const uint32_t sbo = 16u * kp;
+                const int kp = K::kpad(tl.f);
+                const uint32_t sbo = 8u * K::ES * kp;  // 8-row groups
                 const uint32_t a_hi = bfd::smem_u32(smem + C::OFF_A + a * C::A_STAGE);
-                const uint32_t a_lo = a_hi + TC_IMG_MAX;
+                const uint32_t a_lo = a_hi + C::IMG;
                 const uint32_t b_hi = bfd::smem_u32(smem + C::OFF_W + wb * C::W_BUF);
-                const uint32_t b_lo = b_hi + (uint32_t)tc_img_bytes(kp);
+                const uint32_t b_lo = b_hi + (uint32_t)K::img(kp);
                 const uint32_t dt = tmem_base + d * TC_ACC_COLS;
-                for (int s = 0; s < kp / 16; ++s) {
+                auto mma = [&](uint32_t adr, uint32_t bdr, uint32_t acc) {
+                    if constexpr (OPK == OP_TF32)
+                        bfd::umma_tf32(dt, bfd::smem_desc(adr, 128, sbo), bfd::smem_desc(bdr, 128, sbo), IDESC, acc);
+                    else
+                        bfd::umma_f16(dt, bfd::smem_desc(adr, 128, sbo), bfd::smem_desc(bdr, 128, sbo), IDESC, acc);
+                };
+                for (int s = 0; s < kp / K::KSTEP; ++s) {
                     const uint32_t o = 256u * s;  // two 128-byte core matrices along K
-                    bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo), bfd::smem_desc(b_hi + o, 128, sbo),
-                                  IDESC, s > 0 ? 1u : 0u);
+                    mma(a_hi + o, b_hi + o, s > 0 ? 1u : 0u);
                     if (TERMS == 3) {
-                        bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo),
-                                      bfd::smem_desc(b_lo + o, 128, sbo), IDESC, 1u);
-                        bfd::umma_f16(dt, bfd::smem_desc(a_lo + o, 128, sbo),
-                                      bfd::smem_desc(b_hi + o, 128, sbo), IDESC, 1u);
+                        mma(a_hi + o, b_lo + o, 1u);
+                        mma(a_lo + o, b_hi + o, 1u);
                     }
                 }
                 bfd::umma_commit(a_empty(a));
@@ -318,15 +347,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                     }
                     if (j < B_RE) {
                         const uint8_t *raw = smem + C::OFF_RAW + r * TC_RAW_SLOT;
-                        const int kp = kpad_of(f);
+                        const int kp = K::kpad(f);
                         const int row = 64 * blk + j;
-                        uint8_t *dst =
-                            smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
-                        for (int q = q0; q < kp / 8; q += QSTEP) {
-                            float v[8];
+                        uint8_t *dst = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (8 * K::ES * kp) +
+                                       (row & 7) * 16;
+                        constexpr int FPC = 8 / K::ES;  // flows per 16-byte chunk of a row
+                        for (int q = q0; q < kp * K::ES / 16; q += QSTEP) {
+                            float v[2 * FPC];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int k = 4 * q + u;
+                            for (int u = 0; u < FPC; ++u) {
+                                const int k = FPC * q + u;
                                 float2 x = make_float2(0.f, 0.f);
                                 if (k < f) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F + j * 8);
                                 v[2 * u] = x.x;
@@ -334,20 +364,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                             }
                             uint4 hi, lo;
                             uint32_t *h = &hi.x, *l = &lo.x;
+                            if constexpr (OPK == OP_TF32) {
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                if (BF16) {
-                                    h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
-                                    if (TERMS == 3) {
-                                        const float2 back = unpack2_bf16(h[u]);
-                                        l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
+                                for (int u = 0; u < 4; ++u) {
+                                    h[u] = bfd::tf32_rne_bits(v[u]);
+                                    l[u] = bfd::tf32_rne_bits(v[u] - __uint_as_float(h[u]));  // x - hi is exact
+                                }
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    if (OPK == OP_BF16) {
+                                        h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
+                                        if (TERMS == 3) {
+                                            const float2 back = unpack2_bf16(h[u]);
+                                            l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
+                                        }
+                                    } else {
+                                        h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
                                     }
-                                } else {
-                                    h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
                                 }
                             }
                             *reinterpret_cast<uint4 *>(dst + q * 128) = hi;
-                            if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + TC_IMG_MAX + q * 128) = lo;
+                            if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + C::IMG + q * 128) = lo;
                         }
                     }
                     __syncwarp();
@@ -418,52 +456,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     }
 }
 
-template <int TERMS, bool HELD, bool BF16>
+template <int TERMS, bool HELD, int OPK>
 static cudaError_t configure_tc_t() {
-    return cudaFuncSetAttribute(bf_tc_kernel<TERMS, HELD, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcCfg<TERMS, HELD>::SMEM);
+    return cudaFuncSetAttribute(bf_tc_kernel<TERMS, HELD, OPK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<TERMS, HELD, OPK>::SMEM);
 }
 
-template <int TERMS, bool HELD, bool BF16>
+template <int TERMS, bool HELD, int OPK>
 static cudaError_t launch_tc_t(const KParams &p, int n_cta, cudaStream_t stream) {
     // Programmatic stream serialization: this launch may begin its prologue
     // while the previous kernel on the stream finishes (see grid_dep_wait).
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_cta);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = TcCfg<TERMS, HELD>::SMEM;
+    cfg.dynamicSmemBytes = TcCfg<TERMS, HELD, OPK>::SMEM;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, bf_tc_kernel<TERMS, HELD, BF16>, p);
+    return cudaLaunchKernelEx(&cfg, bf_tc_kernel<TERMS, HELD, OPK>, p);
 }
 
 // Raise every instance's dynamic shared-memory limit (once, before launches).
 cudaError_t configure_tc() {
     cudaError_t e;
-    if ((e = configure_tc_t<3, true, true>()) != cudaSuccess) return e;
-    if ((e = configure_tc_t<3, false, true>()) != cudaSuccess) return e;
-    if ((e = configure_tc_t<1, true, true>()) != cudaSuccess) return e;
-    if ((e = configure_tc_t<1, false, true>()) != cudaSuccess) return e;
-    if ((e = configure_tc_t<1, true, false>()) != cudaSuccess) return e;
-    return configure_tc_t<1, false, false>();
+    if ((e = configure_tc_t<3, true, OP_BF16>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<3, false, OP_BF16>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, true, OP_BF16>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, false, OP_BF16>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, true, OP_FP16>()) != cudaSuccess) return e;
+    if ((e = configure_tc_t<1, false, OP_FP16>()) != cudaSuccess) return e;
+    return configure_tc_t<3, false, OP_TF32>();
 }
 
-// prec: BF_BF16, BF_FP16 or BF_BF16X3.
+// prec: BF_BF16, BF_FP16, BF_BF16X3 or BF_TF32X3 (complex64 S only).
 cudaError_t launch_tc(int prec, bool held, const KParams &p, int n_cta, cudaStream_t stream) {
-    if (prec == BF_BF16X3) return held ? launch_tc_t<3, true, true>(p, n_cta, stream)
-                                       : launch_tc_t<3, false, true>(p, n_cta, stream);
-    if (prec == BF_BF16) return held ? launch_tc_t<1, true, true>(p, n_cta, stream)
-                                     : launch_tc_t<1, false, true>(p, n_cta, stream);
-    return held ? launch_tc_t<1, true, false>(p, n_cta, stream) : launch_tc_t<1, false, false>(p, n_cta, stream);
+    if (prec == BF_TF32X3) return launch_tc_t<3, false, OP_TF32>(p, n_cta, stream);
+    if (prec == BF_BF16X3) return held ? launch_tc_t<3, true, OP_BF16>(p, n_cta, stream)
+                                       : launch_tc_t<3, false, OP_BF16>(p, n_cta, stream);
+    if (prec == BF_BF16) return held ? launch_tc_t<1, true, OP_BF16>(p, n_cta, stream)
+                                     : launch_tc_t<1, false, OP_BF16>(p, n_cta, stream);
+    return held ? launch_tc_t<1, true, OP_FP16>(p, n_cta, stream) : launch_tc_t<1, false, OP_FP16>(p, n_cta, stream);
 }
 
 int tc_smem_bytes(int prec, bool held) {
-    if (prec == BF_BF16X3) return held ? TcCfg<3, true>::SMEM : TcCfg<3, false>::SMEM;
-    return held ? TcCfg<1, true>::SMEM : TcCfg<1, false>::SMEM;
+    if (prec == BF_TF32X3) return TcCfg<3, false, OP_TF32>::SMEM;
+    if (prec == BF_BF16X3) return held ? TcCfg<3, true, OP_BF16>::SMEM : TcCfg<3, false, OP_BF16>::SMEM;
+    return held ? TcCfg<1, true, OP_BF16>::SMEM : TcCfg<1, false, OP_BF16>::SMEM;
 }
 
 }  // namespace bfi

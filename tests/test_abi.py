@@ -144,8 +144,10 @@ def test_scheduler_rejects_bad_input(bf):
     assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
     ga, n = bf.make_groups([(0, 2, 0, 0)])
     assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 1, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
-    assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32_3M, 1, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
-    assert L.bf_schedule(fa, 2, ga, n, 5, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    for prec in (bf.BF_FP32_3M, bf.BF_TF32X3):  # no held S for these forms
+        assert L.bf_schedule(fa, 2, ga, n, prec, 1, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    assert L.bf_schedule(fa, 2, ga, n, 6, 0, 4, None, 0, None, ctypes.byref(ncta)) == -bf.BF_EINVAL
+    assert L.bf_schedule(fa, 2, ga, n, bf.BF_TF32X3, 0, 1, None, 0, None, ctypes.byref(ncta)) == 1
     # two blocks over up to four CTAs: one block (one tile) each; on one CTA, one two-block tile
     assert L.bf_schedule(fa, 2, ga, n, bf.BF_FP32, 0, 4, None, 0, None, ctypes.byref(ncta)) == 2
     assert ncta.value == 2

@@ -1,11 +1,11 @@
 """GPU parity of every product form against the FP64 oracle, through the C ABI.
 
 Tolerances (relative Frobenius error over the batch, from the accuracy target
-of the method's reduced-precision study): <= 1e-5 for the FP32 plain form and
-the split-bf16 form, <= 2e-2 for single-pass bf16/fp16 (measured against the
+of the method's reduced-precision study): <= 1e-5 for the FP32 forms and the
+split bf16 / tf32 forms, <= 2e-2 for single-pass bf16/fp16 (measured against the
 unrounded FP64 inputs, so the bound covers the operand rounding). Exact-integer
 inputs (odd-integer QAM, Gaussian-integer W in {-2..2}) make every product and
-partial sum exact in bf16, fp16 and fp32, so there every form must match the
+partial sum exact in bf16, fp16, tf32 and fp32, so there every form must match the
 oracle bit for bit. R is NaN-poisoned before each run, so unwritten elements
 (including f = 0 blocks and ragged tiles) fail.
 """
@@ -26,7 +26,7 @@ TOL_SPLIT = 1e-5
 TOL_SINGLE = 2e-2
 FORMS = [("fp32", bf.BF_FP32, False), ("bf16x3", bf.BF_BF16X3, False), ("bf16x3_held", bf.BF_BF16X3, True),
          ("bf16", bf.BF_BF16, False), ("bf16_held", bf.BF_BF16, True), ("fp16", bf.BF_FP16, False),
-         ("fp16_held", bf.BF_FP16, True), ("fp32_3m", bf.BF_FP32_3M, False)]
+         ("fp16_held", bf.BF_FP16, True), ("fp32_3m", bf.BF_FP32_3M, False), ("tf32x3", bf.BF_TF32X3, False)]
 
 
 @pytest.fixture(scope="module")
@@ -45,11 +45,12 @@ def _ref(batch):
 
 
 # forms checked against the oracle of the complex64-rounded inputs (per-block errors too)
-ACCURATE = (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3)
+ACCURATE = (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3, bf.BF_TF32X3)
 
 
 def _tol(prec):
-    return {bf.BF_FP32: TOL_FP32, bf.BF_FP32_3M: TOL_FP32, bf.BF_BF16X3: TOL_SPLIT}.get(prec, TOL_SINGLE)
+    return {bf.BF_FP32: TOL_FP32, bf.BF_FP32_3M: TOL_FP32, bf.BF_BF16X3: TOL_SPLIT,
+            bf.BF_TF32X3: TOL_SPLIT}.get(prec, TOL_SINGLE)
 
 
 def _assert_close(R, ref, tol, what):
@@ -92,8 +93,8 @@ def test_fullband_scaled(plan, name, prec, held):
     print(f"{name}: rel err {e:.3e}")
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[2], FORMS[4], FORMS[7]],
-                         ids=["fp32", "bf16x3", "bf16x3_held", "bf16_held", "fp32_3m"])
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[2], FORMS[4], FORMS[7], FORMS[8]],
+                         ids=["fp32", "bf16x3", "bf16x3_held", "bf16_held", "fp32_3m", "tf32x3"])
 def test_uneven_scaled(plan, name, prec, held):
     """Uneven f (0..36) per group, geometric group sizes, mixed QAM orders."""
     batch = wl.config_uneven(seed=3, n_blocks=700)
@@ -253,12 +254,12 @@ def test_edge_cases_and_errors(plan):
     with pytest.raises(bf.BfError) as ei:
         bf.bf_apply_batch(plan, S_t.data_ptr() + 4, None, [(100, 1, 0, 0)], bf.BF_FP32, R_t)
     assert ei.value.status == bf.BF_EINVAL
-    for prec in (bf.BF_FP32, bf.BF_FP32_3M):
+    for prec in (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_TF32X3):
         with pytest.raises(bf.BfError) as ei:
-            bf.bf_apply_batch(plan, S_t, R_t, [(100, 1, 0, 0)], prec, R_t)  # the FP32 forms take no scale
+            bf.bf_apply_batch(plan, S_t, R_t, [(100, 1, 0, 0)], prec, R_t)  # no held S for these forms
         assert ei.value.status == bf.BF_EINVAL
     with pytest.raises(bf.BfError) as ei:
-        bf.bf_apply_batch(plan, S_t, None, [(100, 1, 0, 0)], 5, R_t)  # unknown precision
+        bf.bf_apply_batch(plan, S_t, None, [(100, 1, 0, 0)], 6, R_t)  # unknown precision
     assert ei.value.status == bf.BF_EINVAL
     with pytest.raises(bf.BfError) as ei:
         bf.bf_set_precoders(plan, S_t, [37], 0)  # f > f_max
@@ -268,7 +269,7 @@ def test_edge_cases_and_errors(plan):
 
 def test_deterministic(plan):
     batch = wl.config_fullband(seed=6, n_rb=7, n_sym=14)
-    for prec in (bf.BF_FP32, bf.BF_BF16X3, bf.BF_BF16):
+    for prec in (bf.BF_FP32, bf.BF_BF16X3, bf.BF_BF16, bf.BF_TF32X3):
         a = run(plan, batch, prec, torch)
         b = run(plan, batch, prec, torch, set_w=False)
         assert all(np.array_equal(x.view(np.uint64), y.view(np.uint64)) for x, y in zip(a, b))
@@ -304,8 +305,8 @@ def test_autotune_keeps_results_and_round_trips(plan, tmp_path):
         bf.bf_plan_destroy(other)
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4], FORMS[7]],
-                         ids=["fp32", "bf16x3", "bf16_held", "fp32_3m"])
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4], FORMS[7], FORMS[8]],
+                         ids=["fp32", "bf16x3", "bf16_held", "fp32_3m", "tf32x3"])
 def test_uneven_full_size(plan, name, prec, held):
     """The uneven workload at full size (16,384 blocks) in one persistent launch,
     checked in full against the oracle."""
@@ -316,14 +317,14 @@ def test_uneven_full_size(plan, name, prec, held):
     print(f"uneven full size {name}: {e:.3e}")
 
 
-@pytest.mark.parametrize("name,prec", [("bf16x3", bf.BF_BF16X3), ("bf16", bf.BF_BF16)])
+@pytest.mark.parametrize("name,prec", [("bf16x3", bf.BF_BF16X3), ("bf16", bf.BF_BF16), ("tf32x3", bf.BF_TF32X3)])
 def test_uneven_full_size_repeatable(plan, name, prec):
     """Pipeline races show up as a few wrong blocks that change from run to run:
     the full-size uneven batch (1- and 2-block tiles, f from 0 to 36, many
     precoder switches per CTA) must give the same bits five times over."""
     batch = wl.config_uneven()
     first = run(plan, batch, prec, torch, mode="batch")
-    ref = _ref(batch) if prec == bf.BF_BF16X3 else oracle.apply_batch(batch)
+    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
     _assert_close(first, ref, _tol(prec), name)
     for rep in range(4):
         again = run(plan, batch, prec, torch, mode="batch" if rep % 2 else "apply", set_w=False)

@@ -31,10 +31,11 @@ from bfrun import decode_r, rl_view, rl_written_mask, run, run_rl  # noqa: E402
 
 FORMS = [("fp32", bf.BF_FP32, False), ("bf16x3", bf.BF_BF16X3, False), ("bf16x3_held", bf.BF_BF16X3, True),
          ("bf16", bf.BF_BF16, False), ("bf16_held", bf.BF_BF16, True), ("fp16", bf.BF_FP16, False),
-         ("fp16_held", bf.BF_FP16, True), ("fp32_3m", bf.BF_FP32_3M, False)]
+         ("fp16_held", bf.BF_FP16, True), ("fp32_3m", bf.BF_FP32_3M, False), ("tf32x3", bf.BF_TF32X3, False)]
 RTYPES = [("c64", bf.BF_R_C64), ("bf16", bf.BF_R_BF16), ("fp16", bf.BF_R_FP16)]
 U_OUT = {bf.BF_R_C64: 0.0, bf.BF_R_BF16: 2.0 ** -8, bf.BF_R_FP16: 2.0 ** -11}
-TOL = {bf.BF_FP32: 1e-5, bf.BF_FP32_3M: 1e-5, bf.BF_BF16X3: 1e-5, bf.BF_BF16: 2e-2, bf.BF_FP16: 2e-2}
+TOL = {bf.BF_FP32: 1e-5, bf.BF_FP32_3M: 1e-5, bf.BF_BF16X3: 1e-5, bf.BF_TF32X3: 1e-5, bf.BF_BF16: 2e-2,
+       bf.BF_FP16: 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -78,7 +79,8 @@ def test_rl_exact_integers_rounded_bitwise(plan, name, prec, held, rname, rtype)
 
 
 @pytest.mark.parametrize("rname,rtype", RTYPES, ids=[r[0] for r in RTYPES])
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4]], ids=["fp32", "bf16x3", "bf16_held"])
+@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4], FORMS[8]],
+                         ids=["fp32", "bf16x3", "bf16_held", "tf32x3"])
 def test_rl_fullband_scaled_within_tolerance(plan, name, prec, held, rname, rtype):
     """The full-band mix (64x36 precoders, 14 blocks each, 64-QAM) on 40 resource blocks."""
     batch = wl.config_fullband(n_rb=40)

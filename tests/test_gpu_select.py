@@ -67,16 +67,17 @@ def test_crafted_table(plan, tmp_path):
 
 
 def test_measured_choice_full_band(plan):
-    """After tuning the three FP32-accurate forms, the full band (f = 36)
+    """After tuning the four FP32-accurate forms, the full band (f = 36)
     selects the form the measurements make fastest, and its prediction is the
     sum of the tuned per-block costs."""
     batch = wl.config_fullband()
     set_precoders(plan, batch, torch)
     groups = layout(batch).groups
-    for p in (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3):
+    accurate = (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3, bf.BF_TF32X3)
+    for p in accurate:
         bf.bf_autotune(plan, p)
     form, ns = bf.bf_select_form(plan, bf.BF_TARGET_FP32, groups)
     costs = {p: bf.bf_tune_query(plan, p, 36)["ns_per_block"] * batch.total_blocks
-             for p in (bf.BF_FP32, bf.BF_FP32_3M, bf.BF_BF16X3)}
+             for p in accurate}
     assert form == min(costs, key=costs.get) and abs(ns - costs[form]) <= 1e-6 * ns
     print("full band choice:", form, {k: round(v / 1e3, 1) for k, v in costs.items()}, "us")
