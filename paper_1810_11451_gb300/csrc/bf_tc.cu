@@ -23,6 +23,10 @@
 // beforehand. Every kind has the same image structure in bytes: K-major, no
 // swizzle, 8-row x 16-byte core matrices 128 bytes apart along K, 8-row
 // groups 8*kpad*esize bytes apart, and 32 bytes of K per instruction.
+// The tf32 operands are twice as large, so the tf32 form keeps the hi term of
+// S in tensor memory (A from tensor memory, one 32-bit column per K element)
+// and only the lo term in shared memory: two operand stages then fit beside
+// one precoder buffer and four raw slots, and conversion overlaps the MMAs.
 //
 // Warp roles (384 threads, one CTA per SM):
 //   warp 0        bulk-loads S (raw complex64 or held images) into a ring
@@ -79,10 +83,10 @@ constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shar
 #ifndef BF_TC_SINGLE_HELD_STAGES
 #define BF_TC_SINGLE_HELD_STAGES 120
 #endif
-// tf32 split: one precoder buffer and one operand stage of 73,728 B each
-// leave room for four raw slots.
+// tf32 split: one precoder buffer (73,728 B), two lo-term stages (36,864 B
+// each) and four raw slots.
 #ifndef BF_TC_TF32_C64_STAGES
-#define BF_TC_TF32_C64_STAGES 114
+#define BF_TC_TF32_C64_STAGES 124
 #endif
 struct Stages {
     int nw, na, nr;
@@ -115,14 +119,20 @@ struct TcCfg {
     static constexpr int NW = ST.nw;
     static constexpr int NA = ST.na;
     static constexpr int NR = HELD ? 0 : ST.nr;
+    // tf32: the hi term of each operand stage lives in tensor memory
+    static constexpr bool A_TMEM = OPK == OP_TF32;
+    static constexpr int NACC = A_TMEM ? 2 : TC_NACC;  // accumulators
+    static constexpr int TMEM_A0 = NACC * TC_ACC_COLS; // first column of the hi stages (128 apart)
+    static constexpr int TMEM_COLS = A_TMEM ? 512 : NACC * TC_ACC_COLS;
+    static_assert(!A_TMEM || TMEM_A0 + 128 * (NA - 1) + 72 <= 512, "tensor-memory columns");
     static constexpr int W_BUF = W_TERMS * IMG;
-    static constexpr int A_STAGE = A_TERMS * IMG;
+    static constexpr int A_STAGE = (A_TMEM ? 1 : A_TERMS) * IMG;
     static constexpr int OFF_W = 0;
     static constexpr int OFF_A = OFF_W + NW * W_BUF;
     static constexpr int OFF_RAW = OFF_A + NA * A_STAGE;
     static constexpr int OFF_BAR = OFF_RAW + NR * TC_RAW_SLOT;
     // raw full/empty, a full/empty, w full/empty, acc full/empty, drain
-    static constexpr int NBARS = 2 * NR + 2 * NA + 2 * NW + 2 * TC_NACC + 1;
+    static constexpr int NBARS = 2 * NR + 2 * NA + 2 * NW + 2 * NACC + 1;
     static constexpr int SMEM = OFF_BAR + NBARS * 8 + 16;
     static_assert(SMEM <= SMEM_LIMIT, "ring depths exceed the shared memory of one CTA");
     static_assert(HELD || NR >= 2, "a two-block tile needs at least two raw slots");
@@ -165,7 +175,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     auto w_empty = [&](int s) { return bar0 + 8u * (2 * C::NR + 2 * C::NA + C::NW + s); };
     auto acc_full = [&](int s) { return bar0 + 8u * (2 * C::NR + 2 * C::NA + 2 * C::NW + s); };
     auto acc_empty = [&](int s) {
-        return bar0 + 8u * (2 * C::NR + 2 * C::NA + 2 * C::NW + TC_NACC + s);
+        return bar0 + 8u * (2 * C::NR + 2 * C::NA + 2 * C::NW + C::NACC + s);
     };
     const uint32_t drain_bar = bar0 + 8u * (C::NBARS - 1);
 
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
             bfd::mbar_init(w_full(s), 1);
             bfd::mbar_init(w_empty(s), 1);
         }
-        for (int s = 0; s < TC_NACC; ++s) {
+        for (int s = 0; s < C::NACC; ++s) {
             bfd::mbar_init(acc_full(s), 1);
             bfd::mbar_init(acc_empty(s), TC_EPI_WARPS);
         }
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
         bfd::mbar_init_fence();
     }
     if (warp == 1) {
-        bfd::tmem_alloc(bfd::smem_u32(tmem_slot), TC_NACC * TC_ACC_COLS);
+        bfd::tmem_alloc(bfd::smem_u32(tmem_slot), C::TMEM_COLS);
         bfd::tmem_relinquish();
     }
     bfd::tc_fence_before();
@@ -287,9 +297,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                     if (!bfd::mbar_wait(w_full(wb), (nw / C::NW) & 1, abort_flag, p.status)) break;
                     ++nw;
                 }
-                const int a = n % C::NA, d = n % TC_NACC;
+                const int a = n % C::NA, d = n % C::NACC;
                 if (!bfd::mbar_wait(a_full(a), (n / C::NA) & 1, abort_flag, p.status)) break;
-                if (!bfd::mbar_wait(acc_empty(d), ((n / TC_NACC) + 1) & 1, abort_flag, p.status)) break;
+                if (!bfd::mbar_wait(acc_empty(d), ((n / C::NACC) + 1) & 1, abort_flag, p.status)) break;
                 bfd::tc_fence_after();
                 const int kp = K::kpad(tl.f);
                 const uint32_t sbo = 8u * K::ES * kp;  // 8-row groups
@@ -298,18 +308,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                 const uint32_t b_hi = bfd::smem_u32(smem + C::OFF_W + wb * C::W_BUF);
                 const uint32_t b_lo = b_hi + (uint32_t)K::img(kp);
                 const uint32_t dt = tmem_base + d * TC_ACC_COLS;
-                auto mma = [&](uint32_t adr, uint32_t bdr, uint32_t acc) {
-                    if constexpr (OPK == OP_TF32)
-                        bfd::umma_tf32(dt, bfd::smem_desc(adr, 128, sbo), bfd::smem_desc(bdr, 128, sbo), IDESC, acc);
-                    else
-                        bfd::umma_f16(dt, bfd::smem_desc(adr, 128, sbo), bfd::smem_desc(bdr, 128, sbo), IDESC, acc);
-                };
-                for (int s = 0; s < kp / K::KSTEP; ++s) {
-                    const uint32_t o = 256u * s;  // two 128-byte core matrices along K
-                    mma(a_hi + o, b_hi + o, s > 0 ? 1u : 0u);
-                    if (TERMS == 3) {
-                        mma(a_hi + o, b_lo + o, 1u);
-                        mma(a_lo + o, b_hi + o, 1u);
+                if constexpr (C::A_TMEM) {
+                    // hi term of S in tensor memory (8 columns per step), lo term in shared memory
+                    const uint32_t at = tmem_base + C::TMEM_A0 + 128u * a;
+                    const uint32_t a_lo_s = a_hi;  // the shared-memory stage holds the lo term only
+                    for (int s = 0; s < kp / K::KSTEP; ++s) {
+                        const uint32_t o = 256u * s;
+                        bfd::umma_tf32_ts(dt, at + 8u * s, bfd::smem_desc(b_hi + o, 128, sbo), IDESC, s > 0 ? 1u : 0u);
+                        bfd::umma_tf32_ts(dt, at + 8u * s, bfd::smem_desc(b_lo + o, 128, sbo), IDESC, 1u);
+                        bfd::umma_tf32(dt, bfd::smem_desc(a_lo_s + o, 128, sbo), bfd::smem_desc(b_hi + o, 128, sbo),
+                                       IDESC, 1u);
+                    }
+                } else {
+                    for (int s = 0; s < kp / K::KSTEP; ++s) {
+                        const uint32_t o = 256u * s;  // two 128-byte core matrices along K
+                        bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo), bfd::smem_desc(b_hi + o, 128, sbo),
+                                      IDESC, s > 0 ? 1u : 0u);
+                        if (TERMS == 3) {
+                            bfd::umma_f16(dt, bfd::smem_desc(a_hi + o, 128, sbo),
+                                          bfd::smem_desc(b_lo + o, 128, sbo), IDESC, 1u);
+                            bfd::umma_f16(dt, bfd::smem_desc(a_lo + o, 128, sbo),
+                                          bfd::smem_desc(b_hi + o, 128, sbo), IDESC, 1u);
+                        }
                     }
                 }
                 bfd::umma_commit(a_empty(a));
@@ -323,7 +343,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
         }
     } else if (warp >= TC_CONV0 && warp < TC_EPI0) {
         // ---------------- converters (complex64 S -> operand images) ----------------
-        if constexpr (!HELD) {
+        if constexpr (C::A_TMEM) {
+            // tf32: thread -> one row of the two-block operand. A warp may
+            // store only to tensor-memory lanes 32*(warp%4) .. +31, so row =
+            // 32*(warp%4) + lane: block (warp%4)/2, resource element j =
+            // 32*(warp%2) + lane; with more than four converter warps, warps
+            // w and w+4 split the K columns. Each thread rounds its row's
+            // values to hi = tf32(x) and lo = tf32(x - hi), stores hi to the
+            // stage's tensor-memory columns (kk = 2k + re/im) and lo to the
+            // shared-memory image. Every converter warp waits on and releases
+            // both raw slots of every tile, so all move through the ring
+            // together.
+            const int q = warp & 3;
+            const int part = (warp - TC_CONV0) >> 2;
+            constexpr int NPART = TC_CONV_WARPS / 4;
+            const int blk = q >> 1, j = (q & 1) * 32 + lane, row = 32 * q + lane;
+            int n = 0, nb = 0;  // tiles and blocks consumed
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const Tile tl = p.tiles[t];
+                const int f = tl.f;
+                if (f == 0) continue;
+                const int a = n % C::NA;
+                if (!bfd::mbar_wait(a_empty(a), ((n / C::NA) + 1) & 1, abort_flag, p.status)) break;
+                for (int b = 0; b < tl.nblk && ok; ++b)
+                    ok = bfd::mbar_wait(raw_full((nb + b) % C::NR), ((nb + b) / C::NR) & 1, abort_flag, p.status);
+                if (!ok) break;
+                bfd::tc_fence_after();  // the MMAs that read this stage have completed
+                if (blk < tl.nblk) {     // warp-uniform
+                    const uint8_t *raw = smem + C::OFF_RAW + ((nb + blk) % C::NR) * TC_RAW_SLOT + j * 8;
+                    const int kp = K::kpad(f);
+                    uint8_t *lo_row = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (32 * kp) + (row & 7) * 16;
+                    const uint32_t t_hi = tmem_base + ((uint32_t)(32 * q) << 16) + C::TMEM_A0 + 128u * a;
+                    for (int g = part; g < kp / 8; g += NPART) {  // flows 4g .. 4g+3, columns 8g .. 8g+7
+                        uint32_t h[8], l[8];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = 4 * g + u;
+                            float2 x = make_float2(0.f, 0.f);
+                            if (k < f && j < B_RE) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F);
+                            h[2 * u] = bfd::tf32_rne_bits(x.x);
+                            h[2 * u + 1] = bfd::tf32_rne_bits(x.y);
+                            l[2 * u] = bfd::tf32_rne_bits(x.x - __uint_as_float(h[2 * u]));  // x - hi is exact
+                            l[2 * u + 1] = bfd::tf32_rne_bits(x.y - __uint_as_float(h[2 * u + 1]));
+                        }
+                        *reinterpret_cast<uint4 *>(lo_row + (2 * g) * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+                        *reinterpret_cast<uint4 *>(lo_row + (2 * g + 1) * 128) = make_uint4(l[4], l[5], l[6], l[7]);
+                        bfd::tmem_st8(t_hi + 8u * g, h);
+                    }
+                    bfd::tmem_st_wait();
+                }
+                bfd::tc_fence_before();
+                bfd::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    for (int b = 0; b < tl.nblk; ++b) bfd::mbar_arrive(raw_empty((nb + b) % C::NR));
+                    bfd::mbar_arrive(a_full(a));
+                }
+                nb += tl.nblk;
+                ++n;
+            }
+        } else if constexpr (!HELD) {
             // thread -> (resource element j, first K chunk q0); every warp
             // converts part of every block, so all converter warps wait on and
             // release every raw slot in order. (Warps that skipped slots could
@@ -347,16 +427,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                     }
                     if (j < B_RE) {
                         const uint8_t *raw = smem + C::OFF_RAW + r * TC_RAW_SLOT;
-                        const int kp = K::kpad(f);
+                        const int kp = kpad_of(f);
                         const int row = 64 * blk + j;
-                        uint8_t *dst = smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (8 * K::ES * kp) +
-                                       (row & 7) * 16;
-                        constexpr int FPC = 8 / K::ES;  // flows per 16-byte chunk of a row
-                        for (int q = q0; q < kp * K::ES / 16; q += QSTEP) {
-                            float v[2 * FPC];
+                        uint8_t *dst =
+                            smem + C::OFF_A + a * C::A_STAGE + (row >> 3) * (16 * kp) + (row & 7) * 16;
+                        for (int q = q0; q < kp / 8; q += QSTEP) {
+                            float v[8];
 #pragma unroll
-                            for (int u = 0; u < FPC; ++u) {
-                                const int k = FPC * q + u;
+                            for (int u = 0; u < 4; ++u) {
+                                const int k = 4 * q + u;
                                 float2 x = make_float2(0.f, 0.f);
                                 if (k < f) x = *reinterpret_cast<const float2 *>(raw + k * S_BYTES_PER_F + j * 8);
                                 v[2 * u] = x.x;
@@ -364,28 +443,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                             }
                             uint4 hi, lo;
                             uint32_t *h = &hi.x, *l = &lo.x;
-                            if constexpr (OPK == OP_TF32) {
 #pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    h[u] = bfd::tf32_rne_bits(v[u]);
-                                    l[u] = bfd::tf32_rne_bits(v[u] - __uint_as_float(h[u]));  // x - hi is exact
-                                }
-                            } else {
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    if (OPK == OP_BF16) {
-                                        h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
-                                        if (TERMS == 3) {
-                                            const float2 back = unpack2_bf16(h[u]);
-                                            l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
-                                        }
-                                    } else {
-                                        h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
+                            for (int u = 0; u < 4; ++u) {
+                                if (OPK == OP_BF16) {
+                                    h[u] = pack2_bf16(v[2 * u], v[2 * u + 1]);
+                                    if (TERMS == 3) {
+                                        const float2 back = unpack2_bf16(h[u]);
+                                        l[u] = pack2_bf16(v[2 * u] - back.x, v[2 * u + 1] - back.y);
                                     }
+                                } else {
+                                    h[u] = pack2_fp16(v[2 * u], v[2 * u + 1]);
                                 }
                             }
                             *reinterpret_cast<uint4 *>(dst + q * 128) = hi;
-                            if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + C::IMG + q * 128) = lo;
+                            if (TERMS == 3) *reinterpret_cast<uint4 *>(dst + TC_IMG_MAX + q * 128) = lo;
                         }
                     }
                     __syncwarp();
@@ -417,8 +488,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
                     for (int i = 16 * c0; i < 16 * (c0 + NCH); ++i) store_r(rj + i * rs, 0.f, 0.f, p.r_type);
                 continue;
             }
-            const int d = n % TC_NACC;
-            if (!bfd::mbar_wait(acc_full(d), (n / TC_NACC) & 1, abort_flag, p.status)) break;
+            const int d = n % C::NACC;
+            if (!bfd::mbar_wait(acc_full(d), (n / C::NACC) & 1, abort_flag, p.status)) break;
             bfd::tc_fence_after();
             float scale = p.w_scale[tl.prec];
             if (HELD) scale *= p.s_scale[tl.sblk + (blk < tl.nblk ? blk : 0)];
@@ -452,7 +523,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     __syncthreads();
     if (warp == 1) {
         bfd::tc_fence_after();
-        bfd::tmem_dealloc(tmem_base, TC_NACC * TC_ACC_COLS);
+        bfd::tmem_dealloc(tmem_base, C::TMEM_COLS);
     }
 }
 
