@@ -373,6 +373,38 @@ def reduced_leg(torch, bf, plan, batch, ref_d, stream, steps=50):
     return out
 
 
+def scaling_leg(torch, bf, plan, batch, ref_d, stream):
+    """Signal-level study of per-block scaling: the single-pass fp16 and bf16
+    forms on S x 2^e, held (one power-of-two scale per block) against complex64
+    S rounded on chip (no per-block scale). Relative error against the oracle's
+    R x 2^e; null where R is not finite."""
+    from bfrun import layout, set_precoders, to_device_c64
+    set_precoders(plan, batch, torch)
+    lay = layout(batch)
+    Sflat, _ = batch.pack_S()
+    nb = batch.total_blocks
+    R = torch.empty(lay.r_blocks * 64 * 60 * 2, dtype=torch.float32, device="cuda")
+    out = {"blocks": nb, "workload": "256-QAM + noise, f = 36, 6 RB x 14 symbols", "rel_err_by_log2_level": {}}
+    for e in (-24, -16, -8, 0, 8, 16, 24):
+        S = to_device_c64(Sflat * 2.0 ** e, torch)
+        ref_e = ref_d * 2.0 ** e
+        row = {}
+        for name, prec, held in (("fp16_held", bf.BF_FP16, True), ("fp16_onchip", bf.BF_FP16, False),
+                                 ("bf16_held", bf.BF_BF16, True), ("bf16_onchip", bf.BF_BF16, False)):
+            if held:
+                lh = layout(batch, 0, prec)
+                Sq = torch.empty(lh.held_bytes // 4 + 4, dtype=torch.float32, device="cuda")
+                sc = torch.empty(nb, dtype=torch.float32, device="cuda")
+                bf.bf_quantize_symbols(plan, S, lay.groups, prec, Sq, lh.held_off, sc, stream)
+                groups = [(g[0], g[1], lh.held_off[i], g[3]) for i, g in enumerate(lay.groups)]
+                bf.bf_apply_batch(plan, Sq, sc, groups, prec, R, stream)
+            else:
+                bf.bf_apply_batch(plan, S, None, lay.groups, prec, R, stream)
+            row[name] = rel_err(torch, bf, plan, R, ref_e, nb, stream)
+        out["rel_err_by_log2_level"][str(e)] = row
+    return out
+
+
 def fused_output_leg(torch, bf, plan, batch, ref, stream, steps=2000, n_sets=4):
     """The full-band product writing R straight into the per-antenna layout
     the OFDM stage reads (antenna i's 3,822 x 60 resource elements in one
@@ -554,7 +586,7 @@ def main():
     ap.add_argument("--sets", type=int, default=3, help="rotating buffer sets (3 keeps the working set above L2)")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven, reduced-precision and serving legs")
     ap.add_argument("--serving-ttis", type=int, default=20000, help="TTIs of the split-bf16 serving run")
-    ap.add_argument("--legs", default="fused_output,uneven,reduced,filter,serving",
+    ap.add_argument("--legs", default="fused_output,uneven,reduced,scaling,filter,serving",
                     help="comma-separated secondary workloads to run after the headline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -624,10 +656,11 @@ def main():
     b_uneven = wl.config_uneven() if extra and "uneven" in want else None
     b_reduced = wl.config_reduced() if extra and "reduced" in want else None
     b_filter = wl.config_filter_bench() if extra and "filter" in want else None
+    b_scaling = wl.config_reduced(copies=1, n_rb=6, n_sym=14) if extra and "scaling" in want else None
     filter_sample = None
     if rank == 0 and not args.no_cpu:
         cpu, ref = cpu_baseline(batch)
-        refs = cpu_references({"fullband": ref}, {"uneven": b_uneven, "reduced": b_reduced})
+        refs = cpu_references({"fullband": ref}, {"uneven": b_uneven, "reduced": b_reduced, "scaling": b_scaling})
         if b_filter is not None:
             filter_sample = filter_cpu_leg(b_filter)
         ref_full = refs.pop("fullband")
@@ -660,6 +693,10 @@ def main():
         run_leg(legs, "reduced", reduced_leg, torch, bf, plan, b_reduced, ref_d, stream)
         del ref_d
         torch.cuda.empty_cache()
+    if b_scaling is not None and "scaling" in refs:
+        ref_d = to_device_ref(torch, refs.pop("scaling"))
+        run_leg(legs, "scaling", scaling_leg, torch, bf, plan, b_scaling, ref_d, stream)
+        del ref_d
     if b_filter is not None:
         run_leg(legs, "filter", filter_leg, torch, bf, b_filter, filter_sample, stream)
     if extra and "serving" in want:
