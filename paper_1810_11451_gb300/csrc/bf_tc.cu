@@ -1,6 +1,7 @@
 // bf_tc.cu -- tensor-core forms of R = W x S (Sec. III, beamforming equation)
-// on sm_103a: tcgen05.mma with shared-memory operands, FP32 accumulators in
-// tensor memory, bulk (TMA) copies, mbarrier pipelines.
+// on sm_103a: tcgen05.mma with shared-memory operands (for tf32, the A operand's
+// hi term in tensor memory), FP32 accumulators in tensor memory, bulk (TMA)
+// copies, mbarrier pipelines.
 //
 // The complex product as one real GEMM, resource elements on M:
 //   D[j][2i+c] = sum_kk A[j][kk] * B[kk][2i+c],  kk = 2k + c'
@@ -34,8 +35,9 @@
 //   warp 2        bulk-loads each precoder image once per run of tiles
 //   warps 4..7    (complex64 input) convert raw S into the operand ring
 //   warps 8..11   epilogue: tensor memory -> registers -> global R
-// Tensor memory holds four 128-column accumulators so the MMAs of later
-// tiles overlap the epilogue of earlier ones.
+// Tensor memory holds four 128-column accumulators (two for tf32, whose hi
+// operand stages take the other 256 columns) so the MMAs of later tiles
+// overlap the epilogue of earlier ones.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
