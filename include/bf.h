@@ -118,6 +118,17 @@ const char *bf_status_string(bf_status s);
  * Synchronises the device. BF_OK or BF_ETIMEOUT. */
 bf_status bf_device_status(bf_plan plan);
 
+/* Self-test of the failure detection in the kernels' pipelines. Launches one
+ * CTA in which two roles wait, through the same bounded mbarrier wait the
+ * product kernels use, on barriers that nothing completes: the first gives up
+ * after the wait limit (2 s), raises the CTA's abort flag and sets the plan's
+ * device status word; the second, which starts waiting 1 s later, leaves
+ * through the abort flag before its own limit. Nothing faults or hangs and the
+ * context stays usable. Synchronises, then writes to out_host[4]: first role
+ * gave up (1/0), its wait in ms, second role left early (1/0), its wait in
+ * ms. The status word stays set for the next bf_device_status (BF_ETIMEOUT). */
+bf_status bf_selftest_wait_timeout(bf_plan plan, int32_t *out_host);
+
 /* ------------------------------------------------------------------ precoders */
 
 /* Set precoder slots first_id .. first_id+n_prec-1 (Sec. III: W is constant

@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
             "bf_last_error": (c_char_p, [c_void_p]),
             "bf_status_string": (c_char_p, [c_int]),
             "bf_device_status": (c_int, [c_void_p]),
+            "bf_selftest_wait_timeout": (c_int, [c_void_p, POINTER(c_int32)]),
             "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
             "bf_held_block_bytes": (c_int64, [c_int, c_int]),
             "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
@@ -191,6 +192,15 @@ def bf_status_string(s: int) -> str:
 def bf_device_status(plan) -> int:
     """BF_OK, or BF_ETIMEOUT if a kernel gave up on a bounded wait (cleared)."""
     return int(lib().bf_device_status(plan))
+
+
+def bf_selftest_wait_timeout(plan) -> dict:
+    """Run the bounded-wait self-test kernel (about 2 s); the plan's status
+    word is left set (read it with bf_device_status)."""
+    out = (c_int32 * 4)()
+    _check(lib().bf_selftest_wait_timeout(plan, out), plan)
+    return {"gave_up": int(out[0]), "wait_ms": int(out[1]), "left_on_abort": int(out[2]),
+            "abort_wait_ms": int(out[3])}
 
 
 def bf_set_precoders(plan, W_dev, f_list: Sequence[int], first_id: int = 0, stream=None) -> None:

@@ -210,6 +210,22 @@ extern "C" bf_status bf_device_status(bf_plan plan) {
     return BF_OK;
 }
 
+extern "C" bf_status bf_selftest_wait_timeout(bf_plan plan, int32_t *out_host) {
+    if (!plan || !out_host) return bf_fail(plan, BF_EINVAL, "NULL argument");
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    BF_CK(plan, cudaDeviceSynchronize());
+    // ints 4..7 of the 64-byte status block receive the four results
+    int *out_dev = plan->d_status + 4;
+    BF_CK(plan, cudaMemset(out_dev, 0, 4 * sizeof(int)));
+    BF_CK(plan, launch_selftest_wait(plan->d_status, out_dev, nullptr));
+    BF_CK(plan, cudaDeviceSynchronize());
+    int v[4];
+    BF_CK(plan, cudaMemcpy(v, out_dev, sizeof v, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out_host[i] = v[i];
+    return BF_OK;
+}
+
 // ------------------------------------------------------------------ precoders
 static bf_status ensure_slots(bf_plan plan, int need) {
     if (need <= plan->cap) return BF_OK;

@@ -262,6 +262,43 @@ __global__ void __launch_bounds__(256) bf_sum_pairs_kernel(const double *__restr
     }
 }
 
+// ------------------------------------------------------------------ bounded-wait self-test
+// Two roles wait on mbarriers that nothing completes, through the product
+// kernels' bounded wait: thread 0 gives up at the limit and raises the abort
+// flag; thread 32 starts 1 s later and leaves through the flag. out: gave up,
+// its wait (ms), left early, its wait (ms).
+__global__ void bf_selftest_wait_kernel(int *status, int *out) {
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_word;
+    volatile int *abort_flag = &abort_word;
+    if (threadIdx.x == 0) {
+        bfd::mbar_init(bfd::smem_u32(&bar[0]), 1);
+        bfd::mbar_init(bfd::smem_u32(&bar[1]), 1);
+        *abort_flag = 0;
+        bfd::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = bfd::globaltimer();
+        const bool ok = bfd::mbar_wait(bfd::smem_u32(&bar[0]), 0, abort_flag, status);
+        out[0] = ok ? 0 : 1;
+        out[1] = (int)((bfd::globaltimer() - t0) / 1000000ull);
+    } else if (threadIdx.x == 32) {
+        const unsigned long long d0 = bfd::globaltimer();
+        while (bfd::globaltimer() - d0 < bfd::WAIT_LIMIT_NS / 2) {
+        }
+        const unsigned long long t0 = bfd::globaltimer();
+        const bool ok = bfd::mbar_wait(bfd::smem_u32(&bar[1]), 0, abort_flag, status);
+        out[2] = ok ? 0 : 1;
+        out[3] = (int)((bfd::globaltimer() - t0) / 1000000ull);
+    }
+}
+
+cudaError_t launch_selftest_wait(int *status, int *out, cudaStream_t st) {
+    bf_selftest_wait_kernel<<<1, 64, 0, st>>>(status, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_errnorm(const float2 *R, const double2 *Rref, int64_t n_blocks, double *per_block,
                            double *total, int grid, cudaStream_t st) {
     if (n_blocks > 0) {

@@ -26,6 +26,7 @@ cudaError_t launch_precoders(const float2 *W, const PrecJob *jobs, int n_jobs, u
                              cudaStream_t st);
 cudaError_t launch_quantize(int prec, const uint8_t *S, const QGroup *groups, int n_groups, int max_nb,
                             uint8_t *Sq, float *scale_out, cudaStream_t st);
+cudaError_t launch_selftest_wait(int *status, int *out, cudaStream_t st);
 cudaError_t launch_errnorm(const float2 *R, const double2 *Rref, int64_t n_blocks, double *per_block,
                            double *total, int grid, cudaStream_t st);
 

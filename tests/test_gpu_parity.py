@@ -341,3 +341,18 @@ def test_reduced_full_size(plan, name, prec, held):
     ref = _ref(batch) if prec == bf.BF_BF16X3 else oracle.apply_batch(batch)
     e = _assert_close(R, ref, _tol(prec), name)
     print(f"reduced full size {name}: {e:.3e}")
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(plan):
+    """Failure detection without a fault: a wait that nothing completes gives
+    up at its limit (2 s) and sets the device status; a second role leaves
+    through the abort flag before its own limit; the plan then still computes
+    correct results."""
+    assert bf.bf_device_status(plan) == bf.BF_OK
+    r = bf.bf_selftest_wait_timeout(plan)
+    assert r["gave_up"] == 1 and 1900 <= r["wait_ms"] <= 4000, r
+    assert r["left_on_abort"] == 1 and r["abort_wait_ms"] < 1900, r
+    assert bf.bf_device_status(plan) == bf.BF_ETIMEOUT
+    assert bf.bf_device_status(plan) == bf.BF_OK  # read and cleared
+    batch = wl.config_fullband(seed=6, n_rb=3, n_sym=14)
+    _assert_close(run(plan, batch, bf.BF_BF16X3, torch), _ref(batch), TOL_SPLIT, "after the self-test")
