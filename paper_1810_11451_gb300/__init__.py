@@ -428,6 +428,12 @@ class bf_job(ctypes.Structure):
                 ("pad", c_int32), ("S_dev", c_void_p), ("R_dev", c_void_p), ("arrival_ns", c_int64)]
 
 
+class bf_replay_item(ctypes.Structure):
+    """One entry of an arrival schedule for bf_serve_replay."""
+    _fields_ = [("job", bf_job), ("W_dev", c_void_p), ("f_host", POINTER(c_int32)), ("n_prec", c_int32),
+                ("first_id", c_int32)]
+
+
 class bf_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("launches", c_int64),
                 ("rejected_budget", c_int64), ("rejected_full", c_int64), ("budget_waits", c_int64),
@@ -451,6 +457,8 @@ def _serve_sigs(L):
         ("bf_serve_pause", c_int, [c_void_p, c_int32]),
         ("bf_serve_set_budget", c_int, [c_void_p, c_int64]),
         ("bf_serve_get_stats", c_int, [c_void_p, POINTER(bf_serve_stats)]),
+        ("bf_serve_replay", c_int, [c_void_p, POINTER(bf_replay_item), c_int32, c_int64,
+                                    POINTER(ctypes.c_uint64), POINTER(c_int64)]),
     ]:
         fn = getattr(L, name)
         fn.restype = res
@@ -526,6 +534,17 @@ def bf_serve_get_stats(srv) -> dict:
     s = bf_serve_stats()
     _check(_serve_sigs(lib()).bf_serve_get_stats(srv, ctypes.byref(s)))
     return s.as_dict()
+
+
+def bf_serve_replay(srv, items, start_ns: int) -> Tuple[list, int]:
+    """Replay a schedule (a ctypes array of bf_replay_item, arrivals relative
+    to start_ns) in native code; returns (tickets, late submits). The GIL is
+    released during the call."""
+    n = len(items)
+    tickets = (ctypes.c_uint64 * max(1, n))()
+    late = c_int64()
+    _check(_serve_sigs(lib()).bf_serve_replay(srv, items, n, int(start_ns), tickets, ctypes.byref(late)))
+    return [int(tickets[i]) for i in range(n)], int(late.value)
 
 
 class bf_tile(ctypes.Structure):

@@ -416,3 +416,24 @@ extern "C" bf_status bf_serve_get_stats(bf_server srv, bf_serve_stats *out) {
     *out = srv->stats;
     return BF_OK;
 }
+
+extern "C" bf_status bf_serve_replay(bf_server srv, const bf_replay_item *items, int32_t n, int64_t start_ns,
+                                     uint64_t *tickets, int64_t *late) {
+    if (!srv || n < 0 || (n > 0 && (!items || !tickets)))
+        return bf_fail(srv ? srv->plan : nullptr, BF_EINVAL, "bad arguments");
+    int64_t n_late = 0;
+    bf_status s = BF_OK;
+    for (int32_t i = 0; i < n && s == BF_OK; ++i) {
+        const bf_replay_item &it = items[i];
+        if (it.W_dev) s = bf_serve_set_precoders(srv, it.W_dev, it.f_host, it.n_prec, it.first_id);
+        if (s != BF_OK) break;
+        bf_job job = it.job;
+        job.arrival_ns = start_ns + it.job.arrival_ns;
+        while (bf_now_ns() < job.arrival_ns) {
+        }
+        if (bf_now_ns() - job.arrival_ns > 50000) ++n_late;
+        s = bf_submit(srv, &job, &tickets[i]);
+    }
+    if (late) *late = n_late;
+    return s;
+}

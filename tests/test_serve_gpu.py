@@ -56,7 +56,8 @@ def plan():
     bf.bf_plan_destroy(p)
 
 
-@pytest.mark.parametrize("prec,tol", [(bf.BF_FP32, 1e-5), (bf.BF_BF16X3, 1e-5)], ids=["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec,tol", [(bf.BF_FP32, 1e-5), (bf.BF_BF16X3, 1e-5), (bf.BF_TF32X3, 1e-5)],
+                         ids=["fp32", "bf16x3", "tf32x3"])
 def test_alone_equals_in_mix(plan, prec, tol):
     srv = bf.bf_serve_create(plan, n_slots=4, max_batch_jobs=8, hbm_budget_bytes=8 << 30)
     try:
@@ -138,3 +139,19 @@ def test_plan_outlives_its_servers():
     finally:
         bf.bf_serve_destroy(srv)
     bf.bf_plan_destroy(p)
+
+
+def test_replay_drives_the_device_in_real_time():
+    """The serving simulation through the native load generator on the
+    device: 8 cells for 60 TTIs (six precoder epochs) all complete, each
+    latency counted from its scheduled arrival."""
+    from serving_sim import ServingSim
+    p = bf.bf_plan_create(64, 36, 60)
+    sim = ServingSim(p, torch)
+    try:
+        r = sim.run(wl.serving_schedule(n_tti=60), warm_tti=10)
+    finally:
+        sim.close()
+        bf.bf_plan_destroy(p)
+    assert r["jobs"] == 8 * 50 and 0 < r["p50_us"] <= r["p99_us"] <= r["max_us"] < 30_000, r
+    print("replay, 60 TTIs:", {k: r[k] for k in ("p50_us", "p99_us", "max_us", "late_submits")})

@@ -203,3 +203,43 @@ def test_concurrent_submitters(bf):
         assert st["completed"] == 100 and st["submitted"] == 100
     finally:
         bf.bf_serve_destroy(srv)
+
+
+def test_replay_submits_each_job_at_its_arrival(bf):
+    """The native load generator submits item i at start + arrival_i (never
+    early: latency, counted from the scheduled arrival, is at least the
+    device time), applies precoder updates on the way, and counts late
+    submits (a schedule whose start has passed is all late)."""
+    import ctypes
+    srv = bf.bf_serve_create(None, n_slots=4, max_batch_jobs=1, hbm_budget_bytes=1 << 30, fake_device_us=100)
+    try:
+        n = 12
+        ga, ng = bf.make_groups(job_groups(2))
+        f_arr = (ctypes.c_int32 * 1)(8)
+
+        def schedule():
+            items = (bf.bf_replay_item * n)()
+            for i in range(n):
+                it = items[i]
+                it.job.cell, it.job.n_groups, it.job.groups, it.job.prec = i % 3, ng, ga, bf.BF_FP32
+                it.job.S_dev, it.job.R_dev, it.job.arrival_ns = FAKE_S, FAKE_R, 400_000 * i  # every 0.4 ms
+                if i % 4 == 0:  # a precoder update first (a no-op on the fake device)
+                    it.W_dev, it.f_host, it.n_prec, it.first_id = FAKE_S, f_arr, 1, 0
+            return items
+
+        start = bf.bf_now_ns() + 2_000_000
+        tickets, late = bf.bf_serve_replay(srv, schedule(), start)
+        assert bf.bf_now_ns() >= start + 400_000 * (n - 1)
+        assert len(set(tickets)) == n and 0 <= late <= n
+        lats = [bf.bf_wait(srv, t, 5_000_000) for t in tickets]
+        assert all(l >= 100 for l in lats), lats
+        tickets, late = bf.bf_serve_replay(srv, schedule(), bf.bf_now_ns() - 10_000_000)
+        assert late == n
+        for t in tickets:
+            bf.bf_wait(srv, t, 5_000_000)
+        assert bf.bf_serve_get_stats(srv)["completed"] == 2 * n
+        L = bf._serve_sigs(bf.lib())
+        assert L.bf_serve_replay(srv, None, 1, 0, None, None) == bf.BF_EINVAL
+        assert bf.bf_serve_replay(srv, (bf.bf_replay_item * 0)(), 0) == ([], 0)
+    finally:
+        bf.bf_serve_destroy(srv)
