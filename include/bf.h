@@ -145,6 +145,13 @@ bf_status bf_selftest_wait_timeout(bf_plan plan, int32_t *out_host);
 bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_host,
                            int32_t n_prec, int32_t first_id, void *stream);
 
+/* Grow the precoder store to at least n_slots slots now, so that later
+ * bf_set_precoders calls on slots below n_slots never reallocate it (growing
+ * synchronises the device and copies every image, which a latency-bound
+ * caller such as a serving loop should do before it starts). BF_EINVAL for
+ * n_slots < 0 or above 2^24; BF_ENOMEM if the store cannot grow. */
+bf_status bf_reserve_precoders(bf_plan plan, int32_t n_slots);
+
 /* ------------------------------------------------------------------ held symbols */
 
 /* Bytes of one held (pre-encoded) S block for precision prec at f flows:

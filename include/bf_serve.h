@@ -20,8 +20,9 @@
  *
  * Buffers: the caller keeps S and R of each job resident on the device and
  * owns them; they must stay valid until the job is done. Precoder slots are
- * set through bf_serve_set_precoders so that later launches are ordered after
- * the conversion. While a server exists, only the server may use its plan.
+ * set through bf_serve_set_precoders so that later launches that read those
+ * slots are ordered after the conversion (launches reading other slots are
+ * not held back). While a server exists, only the server may use its plan.
  */
 #ifndef BF_SERVE_H
 #define BF_SERVE_H
@@ -35,7 +36,7 @@ extern "C" {
 typedef struct bf_server_s *bf_server;
 
 typedef struct {
-    int32_t n_slots;           /* launches in flight at once (1..16), one stream each      */
+    int32_t n_slots;           /* launches in flight at once (1..8), one stream each       */
     int32_t max_batch_jobs;    /* jobs merged into one launch (>= 1)                       */
     int32_t queue_capacity;    /* submitted but not admitted jobs; BF_EAGAIN beyond        */
     int32_t fake_device_us;    /* 0: real GPU. > 0: no CUDA at all; every launch "runs"
@@ -78,7 +79,8 @@ bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, bf_server *o
 bf_status bf_serve_destroy(bf_server srv, int64_t timeout_us);
 
 /* Set precoder slots like bf_set_precoders; launches admitted after this call
- * returns are ordered after the conversion. */
+ * returns whose jobs read any of these slots are ordered after the
+ * conversion. Consecutive calls do not wait for each other's conversions. */
 bf_status bf_serve_set_precoders(bf_server srv, const void *W_dev, const int32_t *f_host,
                                  int32_t n_prec, int32_t first_id);
 

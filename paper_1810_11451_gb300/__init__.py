@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "bf_device_status": (c_int, [c_void_p]),
             "bf_selftest_wait_timeout": (c_int, [c_void_p, POINTER(c_int32)]),
             "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
+            "bf_reserve_precoders": (c_int, [c_void_p, c_int32]),
             "bf_held_block_bytes": (c_int64, [c_int, c_int]),
             "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
                                             POINTER(c_int64), c_void_p, c_void_p]),
@@ -201,6 +202,10 @@ def bf_selftest_wait_timeout(plan) -> dict:
     _check(lib().bf_selftest_wait_timeout(plan, out), plan)
     return {"gave_up": int(out[0]), "wait_ms": int(out[1]), "left_on_abort": int(out[2]),
             "abort_wait_ms": int(out[3])}
+
+
+def bf_reserve_precoders(plan, n_slots: int) -> None:
+    _check(lib().bf_reserve_precoders(plan, int(n_slots)), plan)
 
 
 def bf_set_precoders(plan, W_dev, f_list: Sequence[int], first_id: int = 0, stream=None) -> None:

@@ -142,7 +142,9 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
             return bf_fail(nullptr, BF_ECUDA, "cudaEventCreate failed");
         }
     }
-    bool ok = cudaEventCreateWithFlags(&p->prep_ev, cudaEventDisableTiming) == cudaSuccess &&
+    bool ok = true;
+    for (auto &b : p->prep) ok = ok && cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok &&
               cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&p->x_in, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&p->x_run, cudaStreamNonBlocking) == cudaSuccess &&
@@ -175,7 +177,7 @@ extern "C" bf_status bf_plan_destroy(bf_plan plan) {
         if (w.ev) cudaEventDestroy(w.ev);
     }
     void *dev_ptrs[] = {plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_tf32x2, plan->w_scale,
-                        plan->d_status, plan->prep_d, plan->en_d};
+                        plan->d_status, plan->en_d};
     for (void *q : dev_ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < BF_XFER_SLOTS; ++i) {
@@ -184,9 +186,12 @@ extern "C" bf_status bf_plan_destroy(bf_plan plan) {
         for (cudaEvent_t e : {plan->x_in_done[i], plan->x_run_done[i], plan->x_out_done[i]})
             if (e) cudaEventDestroy(e);
     }
-    if (plan->prep_h) cudaFreeHost(plan->prep_h);
+    for (auto &b : plan->prep) {
+        if (b.d) cudaFree(b.d);
+        if (b.h) cudaFreeHost(b.h);
+        if (b.ev) cudaEventDestroy(b.ev);
+    }
     if (plan->en_h) cudaFreeHost(plan->en_h);
-    if (plan->prep_ev) cudaEventDestroy(plan->prep_ev);
     if (plan->x_start) cudaEventDestroy(plan->x_start);
     if (plan->x_end) cudaEventDestroy(plan->x_end);
     for (cudaStream_t st : {plan->cap_stream, plan->x_in, plan->x_run, plan->x_out})
@@ -227,6 +232,19 @@ extern "C" bf_status bf_selftest_wait_timeout(bf_plan plan, int32_t *out_host) {
 }
 
 // ------------------------------------------------------------------ precoders
+// The next staging buffer of the ring, with room for `bytes`; waits only if
+// the launch that last read it has not run yet.
+static bf_status prep_stage(bf_plan plan, size_t bytes, StageBuf **out) {
+    StageBuf &b = plan->prep[plan->prep_next];
+    plan->prep_next = (plan->prep_next + 1) % PREP_RING;
+    BF_CK(plan, cudaEventSynchronize(b.ev));
+    bf_status s;
+    if ((s = grow_pinned(plan, &b.h, &b.hcap, bytes)) != BF_OK) return s;
+    if ((s = grow_dev(plan, &b.d, &b.dcap, bytes)) != BF_OK) return s;
+    *out = &b;
+    return BF_OK;
+}
+
 static bf_status ensure_slots(bf_plan plan, int need) {
     if (need <= plan->cap) return BF_OK;
     int ncap = std::max(need, std::max(64, plan->cap * 2));
@@ -269,6 +287,14 @@ static bf_status ensure_slots(bf_plan plan, int need) {
     return BF_OK;
 }
 
+extern "C" bf_status bf_reserve_precoders(bf_plan plan, int32_t n_slots) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (n_slots < 0 || n_slots > (1 << 24)) return bf_fail(plan, BF_EINVAL, "n_slots out of range");
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    return ensure_slots(plan, n_slots);
+}
+
 extern "C" bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_host, int32_t n_prec,
                                       int32_t first_id, void *stream) {
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
@@ -286,11 +312,9 @@ extern "C" bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int
     if ((s = ensure_slots(plan, first_id + n_prec)) != BF_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)n_prec * sizeof(PrecJob);
-    // The staging buffers may still be read by the previous conversion.
-    BF_CK(plan, cudaEventSynchronize(plan->prep_ev));
-    if ((s = grow_pinned(plan, &plan->prep_h, &plan->prep_hcap, bytes)) != BF_OK) return s;
-    if ((s = grow_dev(plan, &plan->prep_d, &plan->prep_cap, bytes)) != BF_OK) return s;
-    PrecJob *jobs = reinterpret_cast<PrecJob *>(plan->prep_h);
+    StageBuf *sb = nullptr;
+    if ((s = prep_stage(plan, bytes, &sb)) != BF_OK) return s;
+    PrecJob *jobs = reinterpret_cast<PrecJob *>(sb->h);
     int64_t off = 0;
     for (int i = 0; i < n_prec; ++i) {
         jobs[i].w_off = off;
@@ -298,11 +322,11 @@ extern "C" bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int
         jobs[i].slot = first_id + i;
         off += (int64_t)N_ANT * f_host[i];
     }
-    BF_CK(plan, cudaMemcpyAsync(plan->prep_d, plan->prep_h, bytes, cudaMemcpyHostToDevice, st));
-    BF_CK(plan, launch_precoders(reinterpret_cast<const float2 *>(W_dev), reinterpret_cast<PrecJob *>(plan->prep_d),
+    BF_CK(plan, cudaMemcpyAsync(sb->d, sb->h, bytes, cudaMemcpyHostToDevice, st));
+    BF_CK(plan, launch_precoders(reinterpret_cast<const float2 *>(W_dev), reinterpret_cast<PrecJob *>(sb->d),
                                  n_prec, plan->w_simt, plan->w_bf16x2, plan->w_fp16, plan->w_tf32x2,
                                  plan->w_scale, st));
-    BF_CK(plan, cudaEventRecord(plan->prep_ev, st));
+    BF_CK(plan, cudaEventRecord(sb->ev, st));
     for (int i = 0; i < n_prec; ++i) plan->f_slot[first_id + i] = f_host[i];
     return BF_OK;
 }
@@ -345,11 +369,10 @@ extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const 
         if (q_off_host[g] < 0 || (q_off_host[g] & 15))
             return bf_fail(plan, BF_EINVAL, "group %d: q_off must be a non-negative multiple of 16", g);
     if ((s = plan_ensure_device(plan)) != BF_OK) return s;
-    BF_CK(plan, cudaEventSynchronize(plan->prep_ev));
     const size_t bytes = (size_t)n_groups * sizeof(QGroup);
-    if ((s = grow_pinned(plan, &plan->prep_h, &plan->prep_hcap, bytes)) != BF_OK) return s;
-    if ((s = grow_dev(plan, &plan->prep_d, &plan->prep_cap, bytes)) != BF_OK) return s;
-    QGroup *q = reinterpret_cast<QGroup *>(plan->prep_h);
+    StageBuf *sb = nullptr;
+    if ((s = prep_stage(plan, bytes, &sb)) != BF_OK) return s;
+    QGroup *q = reinterpret_cast<QGroup *>(sb->h);
     int blk = 0, max_nb = 0;
     for (int g = 0; g < n_groups; ++g) {
         q[g].s_off = groups[g].s_off;
@@ -362,10 +385,10 @@ extern "C" bf_status bf_quantize_symbols(bf_plan plan, const void *S_dev, const 
         max_nb = std::max(max_nb, (int)groups[g].n_blocks);
     }
     cudaStream_t st = (cudaStream_t)stream;
-    BF_CK(plan, cudaMemcpyAsync(plan->prep_d, plan->prep_h, bytes, cudaMemcpyHostToDevice, st));
-    BF_CK(plan, launch_quantize(prec, (const uint8_t *)S_dev, reinterpret_cast<QGroup *>(plan->prep_d), n_groups,
+    BF_CK(plan, cudaMemcpyAsync(sb->d, sb->h, bytes, cudaMemcpyHostToDevice, st));
+    BF_CK(plan, launch_quantize(prec, (const uint8_t *)S_dev, reinterpret_cast<QGroup *>(sb->d), n_groups,
                                 max_nb, (uint8_t *)Sq_dev, scale_dev, st));
-    BF_CK(plan, cudaEventRecord(plan->prep_ev, st));
+    BF_CK(plan, cudaEventRecord(sb->ev, st));
     return BF_OK;
 }
 

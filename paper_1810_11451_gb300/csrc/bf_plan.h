@@ -62,6 +62,15 @@ struct WorkBuf {
     size_t bytes = 0, tiles_bytes = 0;
 };
 
+// Staging of a precoder or quantisation job list: pinned host image, device
+// copy, and the event recorded after the launch that reads it.
+constexpr int PREP_RING = 8;
+struct StageBuf {
+    uint8_t *d = nullptr, *h = nullptr;
+    size_t dcap = 0, hcap = 0;
+    cudaEvent_t ev = nullptr;
+};
+
 }  // namespace bfi
 
 // Host-buffer pipeline: staging slots and the S + R bytes of one chunk.
@@ -89,10 +98,10 @@ struct bf_plan_s {
     bfi::WorkBuf ring[64];  // one per call in flight; also caches repeated lists
     int ring_next = 0;
     bfi::WorkList scratch_wl;
-    // prep staging
-    uint8_t *prep_d = nullptr, *prep_h = nullptr;
-    size_t prep_cap = 0, prep_hcap = 0;
-    cudaEvent_t prep_ev = nullptr;
+    // prep staging: a ring, so that a call waits only for the launch that
+    // last read the buffer it takes (precoder updates come in bursts)
+    bfi::StageBuf prep[bfi::PREP_RING];
+    int prep_next = 0;
     // accuracy report
     double *en_d = nullptr;
     uint8_t *en_h = nullptr;

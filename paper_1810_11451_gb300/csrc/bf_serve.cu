@@ -26,6 +26,7 @@ struct JobRec {
     int cell = 0;
     bf_precision prec = BF_FP32;
     std::vector<bf_group> groups;  // absolute byte addresses in s_off / r_off
+    int32_t slot_lo = 0, slot_hi = 0;  // precoder slots read: [slot_lo, slot_hi)
     int64_t bytes = 0;
     int64_t arrival_ns = 0;
     int64_t done_ns = 0;
@@ -40,6 +41,12 @@ struct Slot {
     bool busy = false;
     int64_t fake_done_ns = 0;
     std::vector<uint64_t> jobs;
+};
+
+// A precoder conversion that later launches reading its slots must follow.
+struct PrepRec {
+    int32_t lo, hi;  // slots [lo, hi)
+    cudaEvent_t ev;
 };
 
 }  // namespace
@@ -60,9 +67,10 @@ struct bf_server_s {
     bf_serve_stats stats{};
     std::mutex plan_mu;  // the plan is used by the dispatcher and bf_serve_set_precoders
     cudaStream_t prep_st = nullptr;
-    cudaEvent_t prep_ev = nullptr;
-    bool prep_used = false;
+    std::vector<PrepRec> prep_pending;  // conversions not yet seen complete (under plan_mu)
+    std::vector<cudaEvent_t> prep_pool;  // their spare events
     std::vector<bf_group> merged;
+    std::vector<std::pair<int32_t, int32_t>> merged_slots;  // slot ranges of the merged jobs
 };
 
 extern "C" int64_t bf_now_ns(void) {
@@ -79,16 +87,34 @@ static int64_t job_bytes(const int *f_slot, const bf_job *job) {
     return b;
 }
 
-// Launch one merged batch on a slot (called without the queue lock).
-static bf_status launch_slot(bf_server srv, Slot &slot, bf_precision prec, const std::vector<bf_group> &groups) {
+// Launch one merged batch on a slot (called without the queue lock). The
+// launch follows every pending precoder conversion whose slots one of its
+// jobs reads, and no other: a cell's next-epoch update does not hold back the
+// other cells' jobs.
+static bf_status launch_slot(bf_server srv, Slot &slot, bf_precision prec, const std::vector<bf_group> &groups,
+                             const std::vector<std::pair<int32_t, int32_t>> &slot_ranges) {
     if (srv->fake) {
         slot.fake_done_ns = bf_now_ns() + (int64_t)srv->cfg.fake_device_us * 1000;
         return BF_OK;
     }
     std::lock_guard<std::mutex> pl(srv->plan_mu);
     bf_plan plan = srv->plan;
-    if (srv->prep_used && cudaStreamWaitEvent(slot.st, srv->prep_ev, 0) != cudaSuccess)
-        return bf_fail(plan, BF_ECUDA, "cudaStreamWaitEvent failed");
+    for (size_t i = 0; i < srv->prep_pending.size();) {
+        PrepRec &r = srv->prep_pending[i];
+        const cudaError_t e = cudaEventQuery(r.ev);
+        if (e == cudaSuccess) {  // complete: nothing to order after
+            srv->prep_pool.push_back(r.ev);
+            r = srv->prep_pending.back();
+            srv->prep_pending.pop_back();
+            continue;
+        }
+        if (e != cudaErrorNotReady) return bf_fail(plan, BF_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+        bool reads = false;
+        for (const auto &sr : slot_ranges) reads = reads || (sr.first < r.hi && r.lo < sr.second);
+        if (reads && cudaStreamWaitEvent(slot.st, r.ev, 0) != cudaSuccess)
+            return bf_fail(plan, BF_ECUDA, "cudaStreamWaitEvent failed");
+        ++i;
+    }
     // S and R bases are 0: the groups carry absolute device addresses, so jobs
     // with different buffers share one launch.
     bf_status s = enqueue_apply(plan, nullptr, nullptr, groups.data(), (int32_t)groups.size(), prec, nullptr,
@@ -175,10 +201,12 @@ static void dispatcher(bf_server srv) {
                 srv->queue.pop_front();
             }
             srv->merged.clear();
+            srv->merged_slots.clear();
             for (uint64_t t : take) {
                 JobRec &j = srv->jobs[t];
                 j.state = RUNNING;
                 srv->merged.insert(srv->merged.end(), j.groups.begin(), j.groups.end());
+                srv->merged_slots.emplace_back(j.slot_lo, j.slot_hi);
             }
             srv->inflight_bytes += add;
             srv->stats.max_inflight_bytes = std::max(srv->stats.max_inflight_bytes, srv->inflight_bytes);
@@ -186,8 +214,10 @@ static void dispatcher(bf_server srv) {
             free_slot->jobs = take;
             std::vector<bf_group> groups;
             groups.swap(srv->merged);
+            std::vector<std::pair<int32_t, int32_t>> ranges;
+            ranges.swap(srv->merged_slots);
             lk.unlock();
-            const bf_status st = launch_slot(srv, *free_slot, prec, groups);
+            const bf_status st = launch_slot(srv, *free_slot, prec, groups, ranges);
             lk.lock();
             srv->stats.launches++;
             srv->stats.max_jobs_per_launch = std::max(srv->stats.max_jobs_per_launch, (int32_t)take.size());
@@ -242,8 +272,7 @@ extern "C" bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, b
             delete s;
             return st;
         }
-        bool ok = cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&s->prep_ev, cudaEventDisableTiming) == cudaSuccess;
+        bool ok = cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking) == cudaSuccess;
         for (Slot &sl : s->slots)
             ok = ok && cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
@@ -254,7 +283,6 @@ extern "C" bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, b
                 if (sl.ev) cudaEventDestroy(sl.ev);
             }
             if (s->prep_st) cudaStreamDestroy(s->prep_st);
-            if (s->prep_ev) cudaEventDestroy(s->prep_ev);
             delete s;
             return bf_fail(plan, BF_ECUDA, "stream/event creation failed");
         }
@@ -286,7 +314,8 @@ extern "C" bf_status bf_serve_destroy(bf_server srv, int64_t timeout_us) {
         }
         cudaStreamSynchronize(srv->prep_st);
         cudaStreamDestroy(srv->prep_st);
-        cudaEventDestroy(srv->prep_ev);
+        for (const PrepRec &r : srv->prep_pending) cudaEventDestroy(r.ev);
+        for (cudaEvent_t e : srv->prep_pool) cudaEventDestroy(e);
         cudaGetLastError();
     }
     if (srv->plan) srv->plan->servers--;
@@ -300,10 +329,19 @@ extern "C" bf_status bf_serve_set_precoders(bf_server srv, const void *W_dev, co
     if (srv->fake) return BF_OK;
     std::lock_guard<std::mutex> pl(srv->plan_mu);
     bf_status s = bf_set_precoders(srv->plan, W_dev, f_host, n_prec, first_id, srv->prep_st);
-    if (s != BF_OK) return s;
-    if (cudaEventRecord(srv->prep_ev, srv->prep_st) != cudaSuccess)
+    if (s != BF_OK || n_prec == 0) return s;
+    cudaEvent_t ev = nullptr;
+    if (!srv->prep_pool.empty()) {
+        ev = srv->prep_pool.back();
+        srv->prep_pool.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        return bf_fail(srv->plan, BF_ECUDA, "cudaEventCreate failed");
+    }
+    if (cudaEventRecord(ev, srv->prep_st) != cudaSuccess) {
+        srv->prep_pool.push_back(ev);
         return bf_fail(srv->plan, BF_ECUDA, "cudaEventRecord failed");
-    srv->prep_used = true;
+    }
+    srv->prep_pending.push_back({first_id, first_id + n_prec, ev});
     return BF_OK;
 }
 
@@ -327,6 +365,8 @@ extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticke
             a.s_off += (int64_t)(uintptr_t)job->S_dev;
             a.r_off += (int64_t)(uintptr_t)job->R_dev;
             rec.groups.push_back(a);
+            if (g == 0 || gr.prec_id < rec.slot_lo) rec.slot_lo = gr.prec_id;
+            if (g == 0 || gr.prec_id + 1 > rec.slot_hi) rec.slot_hi = gr.prec_id + 1;
         }
         rec.bytes = srv->fake ? 0 : job_bytes(f_slot, job);
         if (srv->fake)

@@ -356,3 +356,16 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(plan):
     assert bf.bf_device_status(plan) == bf.BF_OK  # read and cleared
     batch = wl.config_fullband(seed=6, n_rb=3, n_sym=14)
     _assert_close(run(plan, batch, bf.BF_BF16X3, torch), _ref(batch), TOL_SPLIT, "after the self-test")
+
+
+def test_reserve_precoders(plan):
+    """A reserved precoder store takes slots up to the reservation without
+    growing; a reservation below the current size changes nothing."""
+    bf.bf_reserve_precoders(plan, 6000)
+    bf.bf_reserve_precoders(plan, 10)
+    batch = wl.config_small(seed=1, n_blocks=5, f=5)
+    _assert_close(run(plan, batch, bf.BF_FP32, torch, slot_base=5999), _ref(batch), TOL_FP32, "slot 5999")
+    for bad in (-1, (1 << 24) + 1):
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_reserve_precoders(plan, bad)
+        assert ei.value.status == bf.BF_EINVAL
