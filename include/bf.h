@@ -152,6 +152,14 @@ bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_hos
  * n_slots < 0 or above 2^24; BF_ENOMEM if the store cannot grow. */
 bf_status bf_reserve_precoders(bf_plan plan, int32_t n_slots);
 
+/* Size every buffer of the plan's work-list ring for batches of up to
+ * max_blocks blocks now. A call whose work list outgrows a ring buffer
+ * otherwise allocates a bigger one on the spot (pinned host and device
+ * memory; the old one is kept until the plan is destroyed, so nothing
+ * synchronises the device); a serving loop reserves its largest merged
+ * launch before it starts. BF_EINVAL for max_blocks < 0 or above 2^30. */
+bf_status bf_reserve_worklists(bf_plan plan, int64_t max_blocks);
+
 /* ------------------------------------------------------------------ held symbols */
 
 /* Bytes of one held (pre-encoded) S block for precision prec at f flows:

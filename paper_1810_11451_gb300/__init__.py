@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             "bf_selftest_wait_timeout": (c_int, [c_void_p, POINTER(c_int32)]),
             "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
             "bf_reserve_precoders": (c_int, [c_void_p, c_int32]),
+            "bf_reserve_worklists": (c_int, [c_void_p, c_int64]),
             "bf_held_block_bytes": (c_int64, [c_int, c_int]),
             "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
                                             POINTER(c_int64), c_void_p, c_void_p]),
@@ -206,6 +207,10 @@ def bf_selftest_wait_timeout(plan) -> dict:
 
 def bf_reserve_precoders(plan, n_slots: int) -> None:
     _check(lib().bf_reserve_precoders(plan, int(n_slots)), plan)
+
+
+def bf_reserve_worklists(plan, max_blocks: int) -> None:
+    _check(lib().bf_reserve_worklists(plan, int(max_blocks)), plan)
 
 
 def bf_set_precoders(plan, W_dev, f_list: Sequence[int], first_id: int = 0, stream=None) -> None:

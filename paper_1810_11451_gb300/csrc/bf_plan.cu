@@ -46,13 +46,21 @@ bf_status plan_ensure_device(bf_plan plan) {
     return BF_OK;
 }
 
+// Grow a device buffer to at least `need` bytes (doubling). The old buffer is
+// freed after a device synchronisation, or with `retire` kept until the plan
+// is destroyed, so that a caller on a latency-bound path never synchronises
+// the device (its last reader must have finished).
 template <typename T>
-static bf_status grow_dev(bf_plan plan, T **p, size_t *cap, size_t need) {
+static bf_status grow_dev(bf_plan plan, T **p, size_t *cap, size_t need, bool retire = false) {
     if (need <= *cap) return BF_OK;
     size_t n = std::max(need, *cap * 2);
     if (*p) {
-        BF_CK(plan, cudaDeviceSynchronize());
-        BF_CK(plan, cudaFree(*p));
+        if (retire) {
+            plan->retired_dev.push_back(*p);
+        } else {
+            BF_CK(plan, cudaDeviceSynchronize());
+            BF_CK(plan, cudaFree(*p));
+        }
         *p = nullptr;
         *cap = 0;
     }
@@ -65,11 +73,13 @@ static bf_status grow_dev(bf_plan plan, T **p, size_t *cap, size_t need) {
     return BF_OK;
 }
 
-static bf_status grow_pinned(bf_plan plan, uint8_t **p, size_t *cap, size_t need) {
+// The same for pinned host memory.
+static bf_status grow_pinned(bf_plan plan, uint8_t **p, size_t *cap, size_t need, bool retire = false) {
     if (need <= *cap) return BF_OK;
     size_t n = std::max(need, *cap * 2);
     if (*p) {
-        BF_CK(plan, cudaFreeHost(*p));
+        if (retire) plan->retired_host.push_back(*p);
+        else BF_CK(plan, cudaFreeHost(*p));
         *p = nullptr;
         *cap = 0;
     }
@@ -191,6 +201,8 @@ extern "C" bf_status bf_plan_destroy(bf_plan plan) {
         if (b.h) cudaFreeHost(b.h);
         if (b.ev) cudaEventDestroy(b.ev);
     }
+    for (void *q : plan->retired_dev) cudaFree(q);
+    for (uint8_t *q : plan->retired_host) cudaFreeHost(q);
     if (plan->en_h) cudaFreeHost(plan->en_h);
     if (plan->x_start) cudaEventDestroy(plan->x_start);
     if (plan->x_end) cudaEventDestroy(plan->x_end);
@@ -239,8 +251,8 @@ static bf_status prep_stage(bf_plan plan, size_t bytes, StageBuf **out) {
     plan->prep_next = (plan->prep_next + 1) % PREP_RING;
     BF_CK(plan, cudaEventSynchronize(b.ev));
     bf_status s;
-    if ((s = grow_pinned(plan, &b.h, &b.hcap, bytes)) != BF_OK) return s;
-    if ((s = grow_dev(plan, &b.d, &b.dcap, bytes)) != BF_OK) return s;
+    if ((s = grow_pinned(plan, &b.h, &b.hcap, bytes, true)) != BF_OK) return s;
+    if ((s = grow_dev(plan, &b.d, &b.dcap, bytes, true)) != BF_OK) return s;
     *out = &b;
     return BF_OK;
 }
@@ -284,6 +296,23 @@ static bf_status ensure_slots(bf_plan plan, int need) {
     plan->w_scale = nsc;
     plan->f_slot.resize(ncap, -1);
     plan->cap = ncap;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_reserve_worklists(bf_plan plan, int64_t max_blocks) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (max_blocks < 0 || max_blocks > (int64_t)1 << 30) return bf_fail(plan, BF_EINVAL, "max_blocks out of range");
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    // at most one tile per block, and one range start per CTA of any form
+    const size_t bytes = (size_t)max_blocks * sizeof(Tile) + (size_t)(plan->sm_count * 16 + 1) * sizeof(int32_t);
+    for (auto &w : plan->ring) {
+        if (bytes <= w.hcap && bytes <= w.cap) continue;
+        BF_CK(plan, cudaEventSynchronize(w.ev));
+        w.valid = false;  // the new buffers do not hold the cached list
+        if ((s = grow_pinned(plan, &w.h, &w.hcap, bytes, true)) != BF_OK) return s;
+        if ((s = grow_dev(plan, &w.d, &w.cap, bytes, true)) != BF_OK) return s;
+    }
     return BF_OK;
 }
 
@@ -622,8 +651,8 @@ bf_status enqueue_apply(bf_plan plan, const void *S, const float *scale, const b
         plan->ring_next = (plan->ring_next + 1) % (int)(sizeof(plan->ring) / sizeof(plan->ring[0]));
         BF_CK(plan, cudaEventSynchronize(w.ev));  // its previous launch has finished reading it
         w.valid = false;
-        if ((s = grow_pinned(plan, &w.h, &w.hcap, bytes)) != BF_OK) return s;
-        if ((s = grow_dev(plan, &w.d, &w.cap, bytes)) != BF_OK) return s;
+        if ((s = grow_pinned(plan, &w.h, &w.hcap, bytes, true)) != BF_OK) return s;
+        if ((s = grow_dev(plan, &w.d, &w.cap, bytes, true)) != BF_OK) return s;
         std::memcpy(w.h, wl.tiles.data(), tb);
         std::memcpy(w.h + tb, wl.cta_begin.data(), cb);
         BF_CK(plan, cudaMemcpyAsync(w.d, w.h, bytes, cudaMemcpyHostToDevice, st));

@@ -102,6 +102,9 @@ struct bf_plan_s {
     // last read the buffer it takes (precoder updates come in bursts)
     bfi::StageBuf prep[bfi::PREP_RING];
     int prep_next = 0;
+    // buffers replaced by growth on latency-bound paths, freed with the plan
+    std::vector<void *> retired_dev;
+    std::vector<uint8_t *> retired_host;
     // accuracy report
     double *en_d = nullptr;
     uint8_t *en_h = nullptr;

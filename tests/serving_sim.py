@@ -41,8 +41,10 @@ class ServingSim:
         self.R = [[torch.empty(N_RB_MAX * N_SYM * 64 * 60 * 2, device="cuda") for _ in range(r_ring)]
                   for _ in range(n_cells)]
         torch.cuda.synchronize()
-        # every cell's two precoder banks, allocated before the server starts
+        # every cell's two precoder banks and the largest merged launch,
+        # allocated before the server starts
         bf.bf_reserve_precoders(plan, n_cells * 2 * N_RB_MAX)
+        bf.bf_reserve_worklists(plan, max_batch_jobs * N_RB_MAX * N_SYM)
         self.srv = bf.bf_serve_create(plan, n_slots=n_slots, max_batch_jobs=max_batch_jobs,
                                       queue_capacity=1 << 16, hbm_budget_bytes=budget)
         self._L = bf._serve_sigs(bf.lib())

@@ -369,3 +369,9 @@ def test_reserve_precoders(plan):
         with pytest.raises(bf.BfError) as ei:
             bf.bf_reserve_precoders(plan, bad)
         assert ei.value.status == bf.BF_EINVAL
+    bf.bf_reserve_worklists(plan, 70_000)
+    _assert_close(run(plan, batch, bf.BF_BF16X3, torch, slot_base=5999, set_w=False), _ref(batch), TOL_SPLIT,
+                  "after the work-list reservation")
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_reserve_worklists(plan, -1)
+    assert ei.value.status == bf.BF_EINVAL
