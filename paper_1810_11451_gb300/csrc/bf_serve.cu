@@ -66,6 +66,10 @@ struct bf_server_s {
     std::thread th;
     bf_serve_stats stats{};
     std::mutex plan_mu;  // the plan is used by the dispatcher and bf_serve_set_precoders
+    // the plan's precoder-slot table, read by bf_submit; bf_serve_set_precoders
+    // holds it (inside plan_mu) while it changes the table, so submitters
+    // never wait behind a launch
+    std::mutex slot_mu;
     cudaStream_t prep_st = nullptr;
     std::vector<PrepRec> prep_pending;  // conversions not yet seen complete (under plan_mu)
     std::vector<cudaEvent_t> prep_pool;  // their spare events
@@ -328,7 +332,11 @@ extern "C" bf_status bf_serve_set_precoders(bf_server srv, const void *W_dev, co
     if (!srv) return bf_fail(nullptr, BF_EINVAL, "server is NULL");
     if (srv->fake) return BF_OK;
     std::lock_guard<std::mutex> pl(srv->plan_mu);
-    bf_status s = bf_set_precoders(srv->plan, W_dev, f_host, n_prec, first_id, srv->prep_st);
+    bf_status s;
+    {
+        std::lock_guard<std::mutex> sl(srv->slot_mu);
+        s = bf_set_precoders(srv->plan, W_dev, f_host, n_prec, first_id, srv->prep_st);
+    }
     if (s != BF_OK || n_prec == 0) return s;
     cudaEvent_t ev = nullptr;
     if (!srv->prep_pool.empty()) {
@@ -353,7 +361,7 @@ extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticke
         return bf_fail(srv->plan, BF_EINVAL, "S_dev and R_dev must be non-NULL and 16-byte aligned");
     JobRec rec;
     {
-        std::lock_guard<std::mutex> pl(srv->plan_mu);
+        std::lock_guard<std::mutex> sl(srv->slot_mu);
         const int *f_slot = srv->fake ? nullptr : srv->plan->f_slot.data();
         for (int g = 0; g < job->n_groups; ++g) {
             const bf_group &gr = job->groups[g];
