@@ -112,22 +112,23 @@ bf_status bf_serve_get_stats(bf_server srv, bf_serve_stats *out);
 
 /* One entry of an arrival schedule replayed by bf_serve_replay. */
 typedef struct {
-    bf_job job;                /* arrival_ns relative to the replay's start_ns             */
+    bf_job job;                /* arrival_ns relative to the replay's start_ns; S_dev NULL
+                                  and n_groups 0: no job (a precoder update only)           */
     const void *W_dev;         /* not NULL: bf_serve_set_precoders(srv, W_dev, f_host,     */
-    const int32_t *f_host;     /*   n_prec, first_id) first, before waiting for the arrival */
+    const int32_t *f_host;     /*   n_prec, first_id) at the item's time, before its job   */
     int32_t n_prec;
     int32_t first_id;
 } bf_replay_item;
 
 /* Load generator in native code (the cells of Sec. II's continuous mode, each
  * emitting one job per TTI): on the calling thread, takes the items in order,
- * sets the item's precoders if it carries any, waits (spinning on bf_now_ns)
- * until start_ns + job.arrival_ns and submits the job with that arrival time
- * (latency counts from it); tickets[i] receives item i's ticket. Items whose
- * time has passed are submitted at once. *late (may be NULL) receives the
- * number of submits made more than 50 us after their arrival. Stops at the
- * first failing call and returns its status; the tickets of the items before
- * it stay valid. BF_EINVAL for bad arguments. */
+ * waits (spinning on bf_now_ns) until start_ns + job.arrival_ns, sets the
+ * item's precoders if it carries any, then submits its job with that arrival
+ * time (latency counts from it); tickets[i] receives item i's ticket (0 for an
+ * update-only item). Items whose time has passed run at once. *late (may be
+ * NULL) receives the number of jobs submitted more than 50 us after their
+ * arrival. Stops at the first failing call and returns its status; the
+ * tickets of the items before it stay valid. BF_EINVAL for bad arguments. */
 bf_status bf_serve_replay(bf_server srv, const bf_replay_item *items, int32_t n, int64_t start_ns,
                           uint64_t *tickets, int64_t *late);
 

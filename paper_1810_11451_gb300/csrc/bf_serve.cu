@@ -473,12 +473,13 @@ extern "C" bf_status bf_serve_replay(bf_server srv, const bf_replay_item *items,
     bf_status s = BF_OK;
     for (int32_t i = 0; i < n && s == BF_OK; ++i) {
         const bf_replay_item &it = items[i];
-        if (it.W_dev) s = bf_serve_set_precoders(srv, it.W_dev, it.f_host, it.n_prec, it.first_id);
-        if (s != BF_OK) break;
         bf_job job = it.job;
         job.arrival_ns = start_ns + it.job.arrival_ns;
         while (bf_now_ns() < job.arrival_ns) {
         }
+        if (it.W_dev) s = bf_serve_set_precoders(srv, it.W_dev, it.f_host, it.n_prec, it.first_id);
+        tickets[i] = 0;
+        if (s != BF_OK || (!job.S_dev && job.n_groups == 0)) continue;
         if (bf_now_ns() - job.arrival_ns > 50000) ++n_late;
         s = bf_submit(srv, &job, &tickets[i]);
     }

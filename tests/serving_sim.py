@@ -71,34 +71,49 @@ class ServingSim:
             self._groups[key] = g
         return g, n_rb
 
-    def run(self, jobs, warm_tti=20):
+    def run(self, jobs, warm_tti=20, tti_ns=500_000):
         """Submit `jobs` (workloads.ServingJob, sorted by arrival) in real time.
-        Returns a dict of latency percentiles and throughput."""
+        Returns a dict of latency percentiles and throughput. A cell's
+        precoders for an epoch are set half a TTI before the epoch starts, into
+        the bank the previous epoch does not use, spaced 25 us apart across
+        cells (update-only items of the schedule)."""
         srv = self.srv
-        items = (bf.bf_replay_item * len(jobs))()
         f_arrays = {f: (ctypes.c_int32 * N_RB_MAX)(*([f] * N_RB_MAX)) for f in range(1, 37)}
-        epoch_of_cell = {}
+        first = {}  # (cell, epoch) -> (first tti, f)
+        for j in jobs:
+            k = (j.cell, j.epoch)
+            if k not in first or j.tti < first[k][0]:
+                first[k] = (j.tti, j.f)
+        events = [(tti * tti_ns - tti_ns // 2 + cell * 25_000, 0, (cell, epoch, f))
+                  for (cell, epoch), (tti, f) in first.items()]
+        events += [(int(j.arrival_s * 1e9), 1, j) for j in jobs]
+        events.sort(key=lambda e: (e[0], e[1]))
+        items = (bf.bf_replay_item * len(events))()
         ring_pos = [0] * self.n_cells
         blocks = flops = 0
-        for i, j in enumerate(jobs):
+        meta = []
+        for i, (t, kind, x) in enumerate(events):
             it = items[i]
-            if epoch_of_cell.get(j.cell) != j.epoch:
-                # the cell's precoders for this epoch, into the bank not in use
-                it.W_dev, it.f_host = self.W[j.f].data_ptr(), f_arrays[j.f]
-                it.n_prec, it.first_id = N_RB_MAX, self.slot_base(j.cell, j.epoch % 2)
-                epoch_of_cell[j.cell] = j.epoch
+            it.job.arrival_ns = t  # relative to the replay's start
+            if kind == 0:
+                cell, epoch, f = x
+                it.W_dev, it.f_host = self.W[f].data_ptr(), f_arrays[f]
+                it.n_prec, it.first_id = N_RB_MAX, self.slot_base(cell, epoch % 2)
+                continue
+            j = x
             ga, n = self.groups(j.cell, j.epoch % 2, j.n_rb, j.f)
             R = self.R[j.cell][ring_pos[j.cell]]
             ring_pos[j.cell] = (ring_pos[j.cell] + 1) % len(self.R[j.cell])
             it.job.cell, it.job.n_groups, it.job.groups, it.job.prec = j.cell, n, ga, self.prec
             it.job.S_dev, it.job.R_dev = self.S[j.cell].data_ptr(), R.data_ptr()
-            it.job.arrival_ns = int(j.arrival_s * 1e9)  # relative to the replay's start
+            meta.append((i, j))
             if j.tti >= warm_tti:
                 blocks += j.n_rb * N_SYM
                 flops += j.n_rb * N_SYM * 8 * 64 * 60 * j.f
         t0 = bf.bf_now_ns() + 20_000_000  # the schedule starts 20 ms from now
-        tickets, late = bf.bf_serve_replay(srv, items, t0)
-        meta = jobs
+        all_tickets, late = bf.bf_serve_replay(srv, items, t0)
+        tickets = [all_tickets[i] for i, _ in meta]
+        meta = [j for _, j in meta]
         t_last_submit = bf.bf_now_ns()
         lat = []
         for t, j in zip(tickets, meta):

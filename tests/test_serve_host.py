@@ -208,8 +208,9 @@ def test_concurrent_submitters(bf):
 def test_replay_submits_each_job_at_its_arrival(bf):
     """The native load generator submits item i at start + arrival_i (never
     early: latency, counted from the scheduled arrival, is at least the
-    device time), applies precoder updates on the way, and counts late
-    submits (a schedule whose start has passed is all late)."""
+    device time), applies precoder updates on the way (an update-only item
+    gets ticket 0), and counts late submits (a schedule whose start has
+    passed is all late)."""
     import ctypes
     srv = bf.bf_serve_create(None, n_slots=4, max_batch_jobs=1, hbm_budget_bytes=1 << 30, fake_device_us=100)
     try:
@@ -218,7 +219,9 @@ def test_replay_submits_each_job_at_its_arrival(bf):
         f_arr = (ctypes.c_int32 * 1)(8)
 
         def schedule():
-            items = (bf.bf_replay_item * n)()
+            items = (bf.bf_replay_item * (n + 1))()
+            items[n].job.arrival_ns = 400_000 * n  # update only
+            items[n].W_dev, items[n].f_host, items[n].n_prec, items[n].first_id = FAKE_S, f_arr, 1, 0
             for i in range(n):
                 it = items[i]
                 it.job.cell, it.job.n_groups, it.job.groups, it.job.prec = i % 3, ng, ga, bf.BF_FP32
@@ -229,13 +232,15 @@ def test_replay_submits_each_job_at_its_arrival(bf):
 
         start = bf.bf_now_ns() + 2_000_000
         tickets, late = bf.bf_serve_replay(srv, schedule(), start)
-        assert bf.bf_now_ns() >= start + 400_000 * (n - 1)
-        assert len(set(tickets)) == n and 0 <= late <= n
+        assert bf.bf_now_ns() >= start + 400_000 * n
+        assert tickets[n] == 0
+        tickets = tickets[:n]
+        assert len(set(tickets)) == n and 0 not in tickets and 0 <= late <= n
         lats = [bf.bf_wait(srv, t, 5_000_000) for t in tickets]
         assert all(l >= 100 for l in lats), lats
         tickets, late = bf.bf_serve_replay(srv, schedule(), bf.bf_now_ns() - 10_000_000)
         assert late == n
-        for t in tickets:
+        for t in tickets[:n]:
             bf.bf_wait(srv, t, 5_000_000)
         assert bf.bf_serve_get_stats(srv)["completed"] == 2 * n
         L = bf._serve_sigs(bf.lib())
