@@ -546,12 +546,15 @@ def bf_serve_get_stats(srv) -> dict:
     return s.as_dict()
 
 
-def bf_serve_replay(srv, items, start_ns: int) -> Tuple[list, int]:
+def bf_serve_replay(srv, items, start_ns: int, tickets=None) -> Tuple[list, int]:
     """Replay a schedule (a ctypes array of bf_replay_item, arrivals relative
     to start_ns) in native code; returns (tickets, late submits). The GIL is
-    released during the call."""
+    released during the call. `tickets` (optional, a ctypes c_uint64 array
+    of len(items), zeroed) receives each ticket as its job is submitted, so
+    another thread can retire jobs while the replay runs."""
     n = len(items)
-    tickets = (ctypes.c_uint64 * max(1, n))()
+    if tickets is None:
+        tickets = (ctypes.c_uint64 * max(1, n))()
     late = c_int64()
     _check(_serve_sigs(lib()).bf_serve_replay(srv, items, n, int(start_ns), tickets, ctypes.byref(late)))
     return [int(tickets[i]) for i in range(n)], int(late.value)

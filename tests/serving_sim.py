@@ -15,6 +15,8 @@ load generator (`bf_serve_replay`), so no interpreter sits in the timing loop.
 from __future__ import annotations
 
 import ctypes
+import threading
+import time
 
 import numpy as np
 
@@ -110,16 +112,37 @@ class ServingSim:
             if j.tti >= warm_tti:
                 blocks += j.n_rb * N_SYM
                 flops += j.n_rb * N_SYM * 8 * 64 * 60 * j.f
+        # A consumer thread retires each job as it completes, in submission
+        # order, while the replay runs (tickets appear in the shared array as
+        # the jobs are submitted), as a radio's next stage would.
+        tk = (ctypes.c_uint64 * len(events))()
+        lat, err = [], []
+        replay_done = threading.Event()
+
+        def consume():
+            try:
+                for i, j in meta:
+                    while tk[i] == 0:
+                        if replay_done.is_set() and tk[i] == 0:
+                            return  # the replay stopped before this job
+                        time.sleep(20e-6)
+                    v = bf.bf_wait(srv, tk[i], 30_000_000)
+                    if j.tti >= warm_tti:
+                        lat.append(v)
+            except Exception as e:  # reported after the replay
+                err.append(e)
+
+        th = threading.Thread(target=consume)
+        th.start()
         t0 = bf.bf_now_ns() + 20_000_000  # the schedule starts 20 ms from now
-        all_tickets, late = bf.bf_serve_replay(srv, items, t0)
-        tickets = [all_tickets[i] for i, _ in meta]
-        meta = [j for _, j in meta]
-        t_last_submit = bf.bf_now_ns()
-        lat = []
-        for t, j in zip(tickets, meta):
-            v = bf.bf_wait(srv, t, 30_000_000)
-            if j.tti >= warm_tti:
-                lat.append(v)
+        try:
+            _, late = bf.bf_serve_replay(srv, items, t0, tk)
+        finally:
+            replay_done.set()
+            t_last_submit = bf.bf_now_ns()
+            th.join()
+        if err:
+            raise err[0]
         t_end = bf.bf_now_ns()
         stats = bf.bf_serve_get_stats(srv)
         lat = np.array(lat)
