@@ -242,9 +242,11 @@ bf_status bf_apply_batch_rl(bf_plan plan, const void *S_dev, const float *scale_
  * the product runs, R is copied out, pipelined in chunks of groups (S + R
  * of 2 MiB first, doubling up to 32 MiB) over three internal streams (copy
  * in, compute, copy out), so both directions of the host link stay busy.
- * Ordered after
- * `stream`; `stream` is ordered after its completion (synchronise `stream`
- * before reading R_host). Group offsets refer to the host buffers. */
+ * Ordered after `stream`; `stream` is ordered after its completion
+ * (synchronise `stream` before reading R_host). Group offsets refer to the
+ * host buffers. Consecutive calls on different streams (with different host
+ * buffers) pipeline: a call's copy-in overlaps the previous call's copy-out,
+ * the internal staging ring ordering every reuse. */
 bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups,
                               int32_t n_groups, bf_precision prec, void *R_host,
                               void *stream);

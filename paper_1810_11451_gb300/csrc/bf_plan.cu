@@ -787,7 +787,9 @@ extern "C" bf_status bf_batch_destroy(bf_batch batch) {
 // compute (x_run) and copy-out (x_out), over a ring of BF_XFER_SLOTS device
 // staging slots. Each direction of the host link stays busy on its own
 // stream; a slot's S is reused once the kernel that read it has run, its R
-// once the copy-out that read it has finished.
+// once the copy-out that read it has finished -- also across calls, so calls
+// on different user streams pipeline through the three streams (the next
+// call's copy-in runs while this one's copy-out finishes).
 extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const bf_group *groups, int32_t n_groups,
                                          bf_precision prec, void *R_host, void *stream) {
     bf_status s = validate_apply(plan, S_host, nullptr, groups, n_groups, prec, R_host, false);
@@ -820,8 +822,9 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
     max_s = std::max(max_s, cs);
     max_r = std::max(max_r, cr);
     const int n_chunks = (int)cut.size() - 1;
-    const int slots = std::min(n_chunks, BF_XFER_SLOTS);
-    for (int i = 0; i < slots; ++i) {
+    // the slots this call will use, from the ring's current position
+    for (int c = 0; c < std::min(n_chunks, BF_XFER_SLOTS); ++c) {
+        const int i = (plan->x_next + c) % BF_XFER_SLOTS;
         if ((s = grow_dev(plan, &plan->x_s[i], &plan->x_scap[i], (size_t)std::max<int64_t>(max_s, 16))) != BF_OK) return s;
         if ((s = grow_dev(plan, &plan->x_r[i], &plan->x_rcap[i], (size_t)std::max<int64_t>(max_r, 16))) != BF_OK) return s;
     }
@@ -831,10 +834,12 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
     BF_CK(plan, cudaStreamWaitEvent(plan->x_out, plan->x_start, 0));
     std::vector<bf_group> local;
     for (int c = 0; c < n_chunks; ++c) {
-        const int k = c % BF_XFER_SLOTS;
-        const bool reuse = c >= BF_XFER_SLOTS;
-        // copy S in, merging groups that are contiguous in the host buffer
-        if (reuse) BF_CK(plan, cudaStreamWaitEvent(plan->x_in, plan->x_run_done[k], 0));
+        const int k = plan->x_next;
+        plan->x_next = (plan->x_next + 1) % BF_XFER_SLOTS;
+        // copy S in, merging groups that are contiguous in the host buffer,
+        // once the last kernel that read this slot (this call's or an
+        // earlier one's) has run
+        BF_CK(plan, cudaStreamWaitEvent(plan->x_in, plan->x_run_done[k], 0));
         local.clear();
         int64_t so = 0, ro = 0;
         int64_t run_src = -1, run_dst = 0, run_len = 0;
@@ -866,7 +871,7 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
         BF_CK(plan, cudaEventRecord(plan->x_in_done[k], plan->x_in));
         // the product, once S is in and the slot's previous R has left
         BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_in_done[k], 0));
-        if (reuse) BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_out_done[k], 0));
+        BF_CK(plan, cudaStreamWaitEvent(plan->x_run, plan->x_out_done[k], 0));
         if ((s = enqueue_apply(plan, plan->x_s[k], nullptr, local.data(), (int32_t)local.size(), prec, plan->x_r[k],
                                plan->x_run, 0)) != BF_OK)
             return s;

@@ -118,6 +118,7 @@ struct bf_plan_s {
     cudaEvent_t x_in_done[BF_XFER_SLOTS] = {}, x_run_done[BF_XFER_SLOTS] = {}, x_out_done[BF_XFER_SLOTS] = {};
     uint8_t *x_s[BF_XFER_SLOTS] = {}, *x_r[BF_XFER_SLOTS] = {};
     size_t x_scap[BF_XFER_SLOTS] = {}, x_rcap[BF_XFER_SLOTS] = {};
+    int x_next = 0;  // next staging slot (the ring continues across calls)
     int64_t host_chunk_bytes = BF_HOST_CHUNK_BYTES;
     // tuning and counters
     bfi::TuneTable tune;
