@@ -66,7 +66,9 @@ bf_status bf_filter_apply(bf_filter filter, const void *s_dev, int64_t n_sig, vo
 /* The same with s and y in HOST memory (best pinned): blocks are copied in,
  * filtered and copied out in chunks over internal copy-in, compute and
  * copy-out streams. Ordered after `stream`; `stream` is ordered after its
- * completion (synchronise `stream` before reading y_host). */
+ * completion (synchronise `stream` before reading y_host). Consecutive calls
+ * on different streams (with different host buffers) pipeline: the internal
+ * staging ring orders every reuse across calls. */
 bf_status bf_filter_apply_host(bf_filter filter, const void *s_host, int64_t n_sig, void *y_host,
                                void *stream);
 

@@ -313,6 +313,7 @@ struct bf_filter_s {
     cudaEvent_t in_done[3] = {}, run_done[3] = {}, out_done[3] = {};
     float2 *slot_s[3] = {}, *slot_y[3] = {};
     size_t slot_cap = 0;  // blocks per slot
+    int slot_next = 0;    // next slot (the ring continues across calls)
 };
 
 static thread_local std::string g_create_err;
@@ -485,7 +486,9 @@ extern "C" bf_status bf_filter_apply(bf_filter f, const void *s_dev, int64_t n_s
 }
 
 // Chunks grow from 256 blocks (2 MiB in + 2 MiB out) to 2,048 blocks, so that
-// the first copy-out starts early and later chunks amortise the calls.
+// the first copy-out starts early and later chunks amortise the calls. A
+// slot's reuse waits for the kernel and the copy-out that last used it, in
+// this call or an earlier one, so calls on different streams pipeline.
 extern "C" bf_status bf_filter_apply_host(bf_filter f, const void *s_host, int64_t n_sig, void *y_host,
                                           void *stream) {
     bf_status s = ff_check_apply(f, s_host, n_sig, y_host, false);
@@ -514,15 +517,16 @@ extern "C" bf_status bf_filter_apply_host(bf_filter f, const void *s_host, int64
     FF_CK(f, cudaStreamWaitEvent(f->x_out, f->x_start, 0));
     const size_t blk = N * sizeof(float2);
     int64_t done = 0, chunk = FIRST;
-    for (int c = 0; done < n_sig; ++c) {
-        const int k = c % 3;
+    while (done < n_sig) {
+        const int k = f->slot_next;
+        f->slot_next = (f->slot_next + 1) % 3;
         const int64_t nb = std::min<int64_t>(std::min<int64_t>(chunk, (int64_t)f->slot_cap), n_sig - done);
-        if (c >= 3) FF_CK(f, cudaStreamWaitEvent(f->x_in, f->run_done[k], 0));
+        FF_CK(f, cudaStreamWaitEvent(f->x_in, f->run_done[k], 0));
         FF_CK(f, cudaMemcpyAsync(f->slot_s[k], (const uint8_t *)s_host + done * blk, nb * blk, cudaMemcpyHostToDevice,
                                  f->x_in));
         FF_CK(f, cudaEventRecord(f->in_done[k], f->x_in));
         FF_CK(f, cudaStreamWaitEvent(f->x_run, f->in_done[k], 0));
-        if (c >= 3) FF_CK(f, cudaStreamWaitEvent(f->x_run, f->out_done[k], 0));
+        FF_CK(f, cudaStreamWaitEvent(f->x_run, f->out_done[k], 0));
         FF_CK(f, launch_filter(true, f->slot_s[k], f->slot_y[k], nb, f, f->x_run));
         f->launches++;
         FF_CK(f, cudaEventRecord(f->run_done[k], f->x_run));

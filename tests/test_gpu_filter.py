@@ -172,3 +172,30 @@ def test_errors(filt):
         bf.bf_filter_apply(f2, s, 0, s)  # no-op
     finally:
         bf.bf_filter_destroy(f2)
+
+
+def test_host_path_pipelines_across_streams(filt):
+    """Host-buffer calls alternating two streams and two buffer pairs, never
+    synchronised in between: every call's output equals the device path bit
+    for bit."""
+    b = wl.config_filter_tti().rounded()
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    s_d = dev_c64(b.s)
+    y_d = torch.empty_like(s_d)
+    bf.bf_filter_apply(filt, s_d, b.n_sig, y_d)
+    torch.cuda.synchronize()
+    want = y_d.cpu().view(torch.int32)
+    s_h = [torch.from_numpy(np.ascontiguousarray(b.s.astype(np.complex64)).view(np.float32).copy()).pin_memory()
+           for _ in range(2)]
+    y_h = [torch.full_like(s_h[0], float("nan")).pin_memory() for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for rep in range(6):
+        k = rep % 2
+        if rep >= 2:
+            streams[k].synchronize()
+            assert torch.equal(y_h[k].view(torch.int32), want), f"call {rep - 2}"
+            y_h[k].fill_(float("nan"))
+        bf.bf_filter_apply_host(filt, s_h[k], b.n_sig, y_h[k], streams[k])
+    for k in range(2):
+        streams[k].synchronize()
+        assert torch.equal(y_h[k].view(torch.int32), want)
