@@ -106,8 +106,10 @@ bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out);
  * created on the plan (bf_serve_create) has not been destroyed. */
 bf_status bf_plan_destroy(bf_plan plan);
 
-/* Human-readable text of the plan's last error ("" if none). Valid until the
- * next call on the plan. A NULL plan gives the last plan-less error (creation). */
+/* Human-readable text of the plan's last error ("" if none), copied for the
+ * calling thread: valid in that thread until its next bf_last_error call,
+ * also while other threads (a serving engine) use the plan. A NULL plan gives
+ * this thread's last plan-less error (creation). */
 const char *bf_last_error(bf_plan plan);
 
 /* Static name of a status code. */

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,8 +25,12 @@ bf_status bf_fail(bf_plan plan, bf_status s, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (plan) plan->err = buf;
-    else g_err = buf;
+    if (plan) {
+        std::lock_guard<std::mutex> g(plan->err_mu);  // a serving engine fails from two threads
+        plan->err = buf;
+    } else {
+        g_err = buf;
+    }
     return s;
 }
 
@@ -109,7 +114,13 @@ extern "C" const char *bf_status_string(bf_status s) {
     return "BF_UNKNOWN";
 }
 
-extern "C" const char *bf_last_error(bf_plan plan) { return plan ? plan->err.c_str() : g_err.c_str(); }
+extern "C" const char *bf_last_error(bf_plan plan) {
+    if (!plan) return g_err.c_str();
+    static thread_local std::string copy;  // stays valid in this thread while others fail
+    std::lock_guard<std::mutex> g(plan->err_mu);
+    copy = plan->err;
+    return copy.c_str();
+}
 
 extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
     if (!out) return bf_fail(nullptr, BF_EINVAL, "out is NULL");

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -88,6 +89,7 @@ struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
     int simt_resident = 2;  // CTAs of the CUDA-core kernels that fit on one SM (the smaller of the two)
     std::string err;
+    std::mutex err_mu;  // err is written from the caller's and a serving engine's threads
     // precoder store (slots)
     int cap = 0;
     std::vector<int> f_slot;  // -1 = unset
