@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "bf_batch_create_rl": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int,
                                            c_void_p, POINTER(bf_rlayout), POINTER(c_void_p)]),
             "bf_batch_launch": (c_int, [c_void_p, c_void_p]),
+            "bf_batch_set_s_independent": (c_int, [c_void_p, c_int32]),
             "bf_batch_destroy": (c_int, [c_void_p]),
             "bf_errnorm": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
             "bf_plan_launch_count": (c_int64, [c_void_p]),
@@ -271,6 +272,13 @@ def bf_batch_launch(batch, stream=None) -> None:
     st = lib().bf_batch_launch(batch, _stream(stream))
     if st != BF_OK:
         raise BfError(st, "bf_batch_launch failed")
+
+
+def bf_batch_set_s_independent(batch, independent: bool = True) -> None:
+    """Declare that no product launch writes the batch's S (see bf.h)."""
+    st = lib().bf_batch_set_s_independent(batch, 1 if independent else 0)
+    if st != BF_OK:
+        raise BfError(st, "bf_batch_set_s_independent failed")
 
 
 def bf_batch_launch_graph(batch, stream=None) -> None:

@@ -91,6 +91,11 @@ struct KParams {
     int64_t r_block_stride;
     int32_t r_type;
     int32_t r_esize;
+    // 1: no product launch enqueued since the stream's last other operation
+    // writes S or s_scale, so the tensor-core kernel reads S before the
+    // previous grid on the stream completes (only its stores of R wait)
+    int32_t s_independent;
+    int32_t reserved;
 };
 
 constexpr int R_C64 = 0, R_BF16 = 1, R_FP16 = 2;

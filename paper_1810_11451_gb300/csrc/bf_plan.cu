@@ -771,6 +771,13 @@ extern "C" bf_status bf_batch_launch(bf_batch batch, void *stream) {
     return BF_OK;
 }
 
+extern "C" bf_status bf_batch_set_s_independent(bf_batch batch, int32_t independent) {
+    if (!batch) return bf_fail(nullptr, BF_EINVAL, "batch is NULL");
+    if (independent != 0 && independent != 1) return bf_fail(batch->plan, BF_EINVAL, "independent must be 0 or 1");
+    batch->p.s_independent = independent;
+    return BF_OK;
+}
+
 extern "C" bf_status bf_batch_launch_graph(bf_batch batch, void *stream) {
     if (!batch) return bf_fail(nullptr, BF_EINVAL, "batch is NULL");
     bf_plan plan = batch->plan;

@@ -221,9 +221,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bf_tc_kernel(KParams p) {
     // list, which no grid with early release writes: the precoder kernel
     // releases its dependents only by completing and work lists are uploaded
     // by copies, both ordered before this grid could start. So it loads its
-    // first precoder while the previous grid drains.
+    // first precoder while the previous grid drains. When the caller declares
+    // that no product launch writes S (s_independent), only the epilogue --
+    // the one role that writes global memory -- waits: S is loaded, converted
+    // and multiplied while the previous grid finishes.
     bfd::grid_dep_launch();
-    if (warp != 2) bfd::grid_dep_wait();
+    if (warp != 2 && !(p.s_independent && warp < TC_EPI0)) bfd::grid_dep_wait();
     const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == 0) {

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_1810_11451_gb300 as bf  # noqa: E402
-from bfrun import layout, run, set_precoders  # noqa: E402
+from bfrun import layout, run, set_precoders, to_device_c64  # noqa: E402
 
 TOL_FP32 = 1e-5
 TOL_SPLIT = 1e-5
@@ -402,3 +402,44 @@ def test_host_path_pipelines_across_streams(plan):
         streams[k].synchronize()
         got = R_h[k].numpy().view(np.complex64).reshape(-1, 64, 60)
         assert np.array_equal(got.view(np.uint64), np.concatenate(ref).view(np.uint64))
+
+
+@pytest.mark.parametrize("prec", [bf.BF_BF16X3, bf.BF_TF32X3], ids=["bf16x3", "tf32x3"])
+def test_independent_input_keeps_the_r_side_ordered(plan, prec):
+    """A batch declared S-independent loads and multiplies S while the
+    previous launch runs, but its R stores still follow that launch: batch B
+    writes its R over the S that batch A (launched just before, also
+    S-independent: its S comes from a copy) is still reading. Over repeated
+    back-to-back pairs A's R and B's R both equal their results computed alone,
+    bit for bit, and the setter rejects values other than 0 and 1. (A's S is
+    written by B two launches earlier, but the copy in between orders it.)"""
+    a = wl.config_fullband(seed=31, n_rb=40, n_sym=14)  # 560 blocks
+    b = wl.config_fullband(seed=32, n_rb=30, n_sym=14)  # 420 blocks
+    ref_a = run(plan, a, prec, torch)
+    ref_b = run(plan, b, prec, torch, slot_base=300)
+    set_precoders(plan, a, torch)
+    la, lb = layout(a), layout(b, 300)
+    Sa = to_device_c64(a.pack_S()[0], torch)
+    Sb = to_device_c64(b.pack_S()[0], torch)
+    big = torch.zeros(lb.r_blocks * 64 * 60 * 2 + Sa.numel(), dtype=torch.float32, device="cuda")
+    Ra = torch.empty(la.r_blocks * 64 * 60 * 2, dtype=torch.float32, device="cuda")
+    ha = bf.bf_batch_create(plan, big, None, la.groups, prec, Ra)  # A reads S from the front of `big`
+    hb = bf.bf_batch_create(plan, Sb, None, lb.groups, prec, big)  # B writes R over it
+    for h in (ha, hb):
+        bf.bf_batch_set_s_independent(h, True)
+    st = torch.cuda.current_stream()
+    try:
+        for rep in range(20):
+            big[:Sa.numel()].copy_(Sa)  # a copy, not a product launch, writes A's S
+            Ra.fill_(float("nan"))
+            bf.bf_batch_launch(ha, st)
+            bf.bf_batch_launch(hb, st)
+            torch.cuda.synchronize()
+            got_a = Ra.cpu().numpy().view(np.complex64).reshape(-1, 64, 60)
+            got_b = big[:lb.r_blocks * 64 * 60 * 2].cpu().numpy().view(np.complex64).reshape(-1, 64, 60)
+            assert np.array_equal(got_a.view(np.uint64), np.concatenate(ref_a).view(np.uint64)), f"A, pair {rep}"
+            assert np.array_equal(got_b.view(np.uint64), np.concatenate(ref_b).view(np.uint64)), f"B, pair {rep}"
+        assert bf.lib().bf_batch_set_s_independent(ha, 2) == bf.BF_EINVAL
+    finally:
+        bf.bf_batch_destroy(ha)
+        bf.bf_batch_destroy(hb)
