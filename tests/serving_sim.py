@@ -73,12 +73,15 @@ class ServingSim:
             self._groups[key] = g
         return g, n_rb
 
-    def run(self, jobs, warm_tti=20, tti_ns=500_000):
+    def run(self, jobs, warm_tti=20, tti_ns=500_000, sample_every=0, seed=0):
         """Submit `jobs` (workloads.ServingJob, sorted by arrival) in real time.
         Returns a dict of latency percentiles and throughput. A cell's
         precoders for an epoch are set half a TTI before the epoch starts, into
         the bank the previous epoch does not use, spaced 25 us apart across
-        cells (update-only items of the schedule)."""
+        cells (update-only items of the schedule). With sample_every = k > 0,
+        one seeded random block of every k-th job is copied to the host as
+        soon as the job completes (before its R buffer is reused) and returned
+        under "samples" with the indices that locate its W and S."""
         srv = self.srv
         f_arrays = {f: (ctypes.c_int32 * N_RB_MAX)(*([f] * N_RB_MAX)) for f in range(1, 37)}
         first = {}  # (cell, epoch) -> (first tti, f)
@@ -94,6 +97,7 @@ class ServingSim:
         ring_pos = [0] * self.n_cells
         blocks = flops = 0
         meta = []
+        R_of = {}
         for i, (t, kind, x) in enumerate(events):
             it = items[i]
             it.job.arrival_ns = t  # relative to the replay's start
@@ -105,6 +109,7 @@ class ServingSim:
             j = x
             ga, n = self.groups(j.cell, j.epoch % 2, j.n_rb, j.f)
             R = self.R[j.cell][ring_pos[j.cell]]
+            R_of[i] = R
             ring_pos[j.cell] = (ring_pos[j.cell] + 1) % len(self.R[j.cell])
             it.job.cell, it.job.n_groups, it.job.groups, it.job.prec = j.cell, n, ga, self.prec
             it.job.S_dev, it.job.R_dev = self.S[j.cell].data_ptr(), R.data_ptr()
@@ -116,12 +121,15 @@ class ServingSim:
         # order, while the replay runs (tickets appear in the shared array as
         # the jobs are submitted), as a radio's next stage would.
         tk = (ctypes.c_uint64 * len(events))()
-        lat, err = [], []
+        lat, err, samples = [], [], []
         replay_done = threading.Event()
+        rng = np.random.default_rng(seed)
+        picks = {n: int(rng.integers(0, j.n_rb * N_SYM)) for n, (_, j) in enumerate(meta)
+                 if sample_every and n % sample_every == 0}
 
         def consume():
             try:
-                for i, j in meta:
+                for n, (i, j) in enumerate(meta):
                     while tk[i] == 0:
                         if replay_done.is_set() and tk[i] == 0:
                             return  # the replay stopped before this job
@@ -129,6 +137,12 @@ class ServingSim:
                     v = bf.bf_wait(srv, tk[i], 30_000_000)
                     if j.tti >= warm_tti:
                         lat.append(v)
+                    if n in picks:
+                        blk = picks[n]
+                        R = R_of[i]
+                        r = R[blk * 64 * 60 * 2:(blk + 1) * 64 * 60 * 2].cpu().numpy().view(np.complex64)
+                        samples.append({"cell": j.cell, "f": j.f, "rb": blk // N_SYM, "sym": blk % N_SYM,
+                                        "R": r.reshape(64, 60).copy()})
             except Exception as e:  # reported after the replay
                 err.append(e)
 
@@ -158,7 +172,16 @@ class ServingSim:
             "launches": stats["launches"], "max_busy_slots": stats["max_busy_slots"],
             "max_jobs_per_launch": stats["max_jobs_per_launch"], "budget_waits": stats["budget_waits"],
             "max_inflight_bytes": stats["max_inflight_bytes"],
+            **({"samples": samples} if sample_every else {}),
         }
+
+    def sample_inputs(self, smp):
+        """W (64 x f) and S (f x 60) of a sampled block, as complex64 host arrays."""
+        f, rb = smp["f"], smp["rb"]
+        W = self.W[f][rb * 64 * f * 2:(rb + 1) * 64 * f * 2].cpu().numpy().view(np.complex64).reshape(64, f)
+        o = (rb * N_SYM + smp["sym"]) * f * 60 * 2
+        S = self.S[smp["cell"]][o:o + f * 60 * 2].cpu().numpy().view(np.complex64).reshape(f, 60)
+        return W, S
 
     def close(self):
         bf.bf_serve_destroy(self.srv)

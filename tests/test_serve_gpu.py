@@ -141,17 +141,26 @@ def test_plan_outlives_its_servers():
     bf.bf_plan_destroy(p)
 
 
-def test_replay_drives_the_device_in_real_time():
+@pytest.mark.parametrize("prec", [bf.BF_BF16X3, bf.BF_FP32], ids=["bf16x3", "fp32"])
+def test_replay_drives_the_device_in_real_time(prec):
     """The serving simulation through the native load generator on the
-    device: 8 cells for 60 TTIs (six precoder epochs) all complete, each
-    latency counted from its scheduled arrival."""
+    device: 8 cells for 60 TTIs (six precoder epochs, updated between TTIs
+    while other cells' jobs run) all complete, each latency counted from its
+    scheduled arrival; one random block of every 8th job, copied as the job
+    completes, matches the FP64 oracle within 1e-5."""
     from serving_sim import ServingSim
     p = bf.bf_plan_create(64, 36, 60)
-    sim = ServingSim(p, torch)
+    sim = ServingSim(p, torch, prec=prec)
     try:
-        r = sim.run(wl.serving_schedule(n_tti=60), warm_tti=10)
+        r = sim.run(wl.serving_schedule(n_tti=60), warm_tti=10, sample_every=8, seed=4)
+        errs = []
+        for smp in r["samples"]:
+            W, S = sim.sample_inputs(smp)
+            ref = oracle.apply_blocks(W.astype(np.complex128), S[None].astype(np.complex128))[0]
+            errs.append(float(np.linalg.norm(smp["R"] - ref) / np.linalg.norm(ref)))
     finally:
         sim.close()
         bf.bf_plan_destroy(p)
     assert r["jobs"] == 8 * 50 and 0 < r["p50_us"] <= r["p99_us"] <= r["max_us"] < 30_000, r
+    assert len(errs) == 60 and max(errs) <= 1e-5, (len(errs), max(errs))
     print("replay, 60 TTIs:", {k: r[k] for k in ("p50_us", "p99_us", "max_us", "late_submits")})
