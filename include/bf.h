@@ -277,12 +277,11 @@ bf_status bf_batch_destroy(bf_batch batch);
  * library (bf_apply_batch*, bf_batch_launch*) enqueued on the stream since its
  * last other operation (a copy, another kernel, an event wait) writes this
  * batch's S or held-S scales -- as when S lives in its own buffers, filled by
- * copies or other kernels, in a double-buffered pipeline. bf_batch_launch of a
- * tensor-core form then loads, converts and multiplies S while those launches
- * finish; only its stores of R wait for them (R may overlap what they read or
- * write). A wrong declaration gives wrong results. Default 0. The captured
- * graph (bf_batch_launch_graph) and the CUDA-core forms keep the default.
- * BF_EINVAL unless independent is 0 or 1. */
+ * copies or other kernels, in a double-buffered pipeline. bf_batch_launch then
+ * loads S and computes while those launches finish; only its stores of R wait
+ * for them (R may overlap what they read or write). A wrong declaration gives
+ * wrong results. Default 0. The captured graph (bf_batch_launch_graph) keeps
+ * the default. BF_EINVAL unless independent is 0 or 1. */
 bf_status bf_batch_set_s_independent(bf_batch batch, int32_t independent);
 
 /* ------------------------------------------------------------------ scheduler */

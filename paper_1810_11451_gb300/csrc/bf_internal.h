@@ -92,8 +92,8 @@ struct KParams {
     int32_t r_type;
     int32_t r_esize;
     // 1: no product launch enqueued since the stream's last other operation
-    // writes S or s_scale, so the tensor-core kernel reads S before the
-    // previous grid on the stream completes (only its stores of R wait)
+    // writes S or s_scale, so the kernel reads S before the previous grid on
+    // the stream completes (only its stores of R wait)
     int32_t s_independent;
     int32_t reserved;
 };

@@ -102,13 +102,14 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
     }
     __syncthreads();
     // No global memory touched yet: let the next launch start its prologue.
-    // The compute warps (which write R) wait for the previous kernel on the
-    // stream to finish before anything else; the producer waits just before
-    // its first S copy, so its first precoder image loads while the previous
-    // grid drains (precoder images and work lists are never written by a grid
-    // with early release: both are complete before this grid can start).
+    // The previous kernel on the stream may still run. The producer waits for
+    // it just before its first S copy (not at all when the caller declares S
+    // independent of pending product launches), so its first precoder image
+    // loads while the previous grid drains (precoder images and work lists are
+    // never written by a grid with early release: both are complete before
+    // this grid can start). The compute warps read only shared memory and the
+    // work list, so they wait just before their first store of R.
     bfd::grid_dep_launch();
-    if (warp != SIMT_CWARPS) bfd::grid_dep_wait();
     const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == SIMT_CWARPS) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                     ++nW;
                 }
                 if (!dep_done) {
-                    bfd::grid_dep_wait();
+                    if (!p.s_independent) bfd::grid_dep_wait();
                     dep_done = true;
                 }
                 const uint32_t bytes = (uint32_t)(tl.f * S_BYTES_PER_F);
@@ -160,12 +161,19 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
         const int i0 = warp * SIMT_RPW;     // first antenna of this warp
         const int jl = lane < 30 ? lane : 29;  // lanes 30, 31 mirror lane 29 and store nothing
         int nS = 0, nW = 0, wb = 0;
-        bool ok = true;
+        bool ok = true, dep_done = false;
+        auto before_store = [&] {
+            if (!dep_done) {
+                bfd::grid_dep_wait();
+                dep_done = true;
+            }
+        };
         for (int t = t0; t < t1 && ok; ++t) {
             const Tile tl = p.tiles[t];
             const int f = tl.f;
             if (f == 0) {
                 // empty sum: R = 0
+                before_store();
                 if (lane < 30) {
                     for (int b = 0; b < tl.nblk; ++b) {
                         uint8_t *rb = p.R + tl.r_off + (int64_t)b * p.r_block_stride;
@@ -261,6 +269,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
                 __syncwarp();
                 if (lane == 0) bfd::mbar_arrive(s_empty(st));
                 ++nS;
+                before_store();
                 if (lane < 30) {
                     uint8_t *rb = p.R + tl.r_off + (int64_t)b * p.r_block_stride;
 #pragma unroll

@@ -404,7 +404,7 @@ def test_host_path_pipelines_across_streams(plan):
         assert np.array_equal(got.view(np.uint64), np.concatenate(ref).view(np.uint64))
 
 
-@pytest.mark.parametrize("prec", [bf.BF_BF16X3, bf.BF_TF32X3], ids=["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", [bf.BF_BF16X3, bf.BF_TF32X3, bf.BF_FP32], ids=["bf16x3", "tf32x3", "fp32"])
 def test_independent_input_keeps_the_r_side_ordered(plan, prec):
     """A batch declared S-independent loads and multiplies S while the
     previous launch runs, but its R stores still follow that launch: batch B
