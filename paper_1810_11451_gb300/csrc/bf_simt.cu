@@ -108,8 +108,12 @@ __global__ void __launch_bounds__(SIMT_THREADS, SIMT_MIN_CTAS) bf_simt_kernel(KP
     // loads while the previous grid drains (precoder images and work lists are
     // never written by a grid with early release: both are complete before
     // this grid can start). The compute warps read only shared memory and the
-    // work list, so they wait just before their first store of R.
+    // work list: with independent S they start computing at once and wait
+    // just before their first store of R; otherwise they have nothing to do
+    // before S arrives and wait here, blocked rather than polling the S ring
+    // beside the previous grid's CTA on the same SM.
     bfd::grid_dep_launch();
+    if (warp != SIMT_CWARPS && !p.s_independent) bfd::grid_dep_wait();
     const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
 
     if (warp == SIMT_CWARPS) {
