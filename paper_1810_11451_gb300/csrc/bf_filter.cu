@@ -15,11 +15,13 @@
 // The last inverse pass writes y in natural order, coalesced.
 //
 // The 1/N of the inverse is folded into the spectrum (a power of two, exact).
-// Shared-memory bandwidth bounds this kernel, so each pass loads only one or
-// two twiddles per butterfly and forms the others by complex products of at
-// most three factors: pass 2 loads w = e^{-2 pi i k / 256} and w^4 (k = t mod
-// 16, at k and 16 + k), pass 3 loads w = e^{-2 pi i j / 2048} (at TW3 + j).
-// The tables are laid out in thread order, so a warp reads consecutive words.
+// Shared-memory bandwidth limits this kernel, so pass 2 loads only two
+// twiddles per butterfly, w = e^{-2 pi i k / 256} and w^4 (k = t mod 16, at k
+// and 16 + k), and forms the others by complex products of at most three
+// factors. Pass 3's seven twiddles per butterfly depend only on the thread:
+// each thread forms them once from w = e^{-2 pi i j / 2048} (at TW3 + j) and
+// keeps them in registers for all its blocks. The tables are laid out in
+// thread order, so a warp reads consecutive words.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,10 +38,11 @@ namespace bff {
 
 constexpr int N = 2048;
 constexpr int TEAM = 128;                 // threads per block of samples
-// Teams per CTA and CTAs per SM (compile-time knobs). 6 x 1 measured best on
-// the 14,336-block batch (113.6 us; 4 x 1: 116.4, 8 x 1: 121.7 with spills).
+// Teams per CTA and CTAs per SM (compile-time knobs). 4 x 1 with the pass-3
+// twiddles kept in registers measured best on the 14,336-block batch (111.4
+// us; 6 x 1 without them: 113.9, with them it spills: 128.4; 5 x 1: 115.0).
 #ifndef BF_FILTER_TEAMS
-#define BF_FILTER_TEAMS 6
+#define BF_FILTER_TEAMS 4
 #endif
 #ifndef BF_FILTER_CTAS
 #define BF_FILTER_CTAS 1
@@ -187,11 +190,31 @@ __device__ __forceinline__ void team_sync(int team) {
     asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TEAM) : "memory");
 }
 
+// The pass-3 twiddles of thread t, e^{-2 pi i m j / 2048} for m = 1..7 and its
+// two butterflies j = t, t + 128. They depend on t only, so each thread forms
+// them once (from the table's w = e^{-2 pi i j / 2048} by products) and keeps
+// them in registers for every block and both transforms.
+__device__ __forceinline__ void pass3_twiddles(float2 (&w3)[2][8], const float2 *tw, int t) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 w1 = tw[TW3 + t + 128 * h], w2 = cmul(w1, w1), w3_ = cmul(w2, w1), w4 = cmul(w2, w2);
+        w3[h][0] = make_float2(1.f, 0.f);
+        w3[h][1] = w1;
+        w3[h][2] = w2;
+        w3[h][3] = w3_;
+        w3[h][4] = w4;
+        w3[h][5] = cmul(w4, w1);
+        w3[h][6] = cmul(w4, w2);
+        w3[h][7] = cmul(w4, w3_);
+    }
+}
+
 // One transform of the block held as v[m] = x[t + 128 m] (t = thread in the
 // team); leaves v[m] = X[t + 128 m]. E is the team's exchange buffer, tw the
-// per-pass twiddle table.
+// per-pass twiddle table, w3 the thread's pass-3 twiddles.
 template <int DIR>
-__device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2 *tw, int t, int team) {
+__device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2 *tw, const float2 (&w3)[2][8], int t,
+                                        int team) {
     // pass 1: R = 16, Ns = 1 (no twiddles)
     dft16<DIR>(v);
 #pragma unroll
@@ -233,14 +256,8 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
         float2 u[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) u[m] = E[pad(j + 256 * m)];
-        const float2 w1 = tw[TW3 + j], w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
-        u[1] = ctw<DIR>(u[1], w1);
-        u[2] = ctw<DIR>(u[2], w2);
-        u[3] = ctw<DIR>(u[3], w3);
-        u[4] = ctw<DIR>(u[4], w4);
-        u[5] = ctw<DIR>(u[5], cmul(w4, w1));
-        u[6] = ctw<DIR>(u[6], cmul(w4, w2));
-        u[7] = ctw<DIR>(u[7], cmul(w4, w3));
+#pragma unroll
+        for (int m = 1; m < 8; ++m) u[m] = ctw<DIR>(u[m], w3[h][m]);
         dft8<DIR>(u);
         // element j + 256 q = t + 128 (h + 2 q)
 #pragma unroll
@@ -268,6 +285,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
         }
     }
     __syncthreads();
+    float2 w3[2][8];
+    pass3_twiddles(w3, tw, t);
     const long long stride = (long long)gridDim.x * TEAMS;
     long long q = (long long)blockIdx.x * TEAMS + team;
     if (PREFETCH && q < n_sig) prefetch_block(IN, s + q * N, t);
@@ -285,11 +304,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 #pragma unroll
             for (int m = 0; m < 16; ++m) v[m] = sq[t + 128 * m];
         }
-        fft2048<-1>(v, E, tw, t, team);
+        fft2048<-1>(v, E, tw, w3, t, team);
         if (FILTER) {
 #pragma unroll
             for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], Hs[t + 128 * m]);
-            fft2048<1>(v, E, tw, t, team);
+            fft2048<1>(v, E, tw, w3, t, team);
         }
         float2 *yq = y + q * N;
 #pragma unroll
