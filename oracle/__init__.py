@@ -10,11 +10,12 @@ Contents
     `bf_oracle.c` in FP64 (the complex multiply-add written out in reals).
   * `rel_frobenius`, `errnorm_blocks`: the accuracy report -- sum |R - Rref|^2
     and sum |Rref|^2 per block and in total, relative Frobenius error.
-  * `bf16_round`, `fp16_round`, `split_bf16`, `pow2_scale`, `quantize_planes`:
-    the reduced-precision operand encodings (the paper fixes no data type; the
-    readings are: round to nearest even, a power-of-two per-block scale taken
-    from the component-wise max-abs, split x = hi + lo with hi = bf16(x) and
-    lo = bf16(x - hi), all decided in FP32 as the GPU does).
+  * `bf16_round`, `fp16_round`, `tf32_round`, `split_bf16`, `split_tf32`,
+    `pow2_scale`, `quantize_planes`: the reduced-precision operand encodings
+    (the paper fixes no data type; the readings are: round to nearest even, a
+    power-of-two per-block scale taken from the component-wise max-abs, split
+    x = hi + lo with hi = round(x) and lo = round(x - hi), all decided in FP32
+    as the GPU does).
   * `apply_terms`: the FP64 product of already-encoded operands, used to check
     the tensor-core kernels' mechanics tightly.
   * `circular_filter`, `dft`: the fast-convolution filter y = IFFT(MULT(FFT(s)))
@@ -177,6 +178,26 @@ def fp16_bits(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, dtype=np.float32).astype(np.float16).view(np.uint16)
 
 
+def tf32_round(x: np.ndarray) -> np.ndarray:
+    """Round FP32 values to the nearest TF32 value (ties to even), kept as
+    float32 with the 13 dropped fraction bits zero. TF32 keeps the sign, the 8
+    exponent bits and the top 10 fraction bits; the construction is
+    bf16_round's with 13 dropped bits instead of 16. Finite inputs whose
+    rounded value stays finite only."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(13)) & np.uint64(1)
+    u = (u + np.uint64(0xFFF) + lsb) & np.uint64(0xFFFFE000)
+    return u.astype(np.uint32).view(np.float32)
+
+
+def split_tf32(x: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """x ~ hi + lo with hi = tf32(x) and lo = tf32(x - hi); x - hi is exact in FP32."""
+    x = np.asarray(x, dtype=np.float32)
+    hi = tf32_round(x)
+    lo = tf32_round((x - hi).astype(np.float32))
+    return hi, lo
+
+
 def split_bf16(x: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     """x ~ hi + lo with hi = bf16(x) and lo = bf16(x - hi); x - hi is exact in FP32."""
     x = np.asarray(x, dtype=np.float32)
@@ -207,7 +228,7 @@ def block_maxabs(x: np.ndarray) -> float:
 def quantize_planes(x: np.ndarray, prec: str, scaled: bool = True):
     """Encode a complex64 block (or precoder) for a tensor-core path.
 
-    prec: "bf16" | "fp16" | "bf16x3". Returns (scale, planes) where scale is
+    prec: "bf16" | "fp16" | "bf16x3" | "tf32x3". Returns (scale, planes) where scale is
     the power of two that multiplies the encoded values back, and planes is a
     list of (re, im) float32 arrays: one pair for single pass, (hi, lo) pairs
     for the split form. With scaled=False the scale is 1."""
@@ -223,6 +244,10 @@ def quantize_planes(x: np.ndarray, prec: str, scaled: bool = True):
     if prec == "bf16x3":
         rh, rl = split_bf16(re)
         ih, il = split_bf16(im)
+        return s, [(rh, ih), (rl, il)]
+    if prec == "tf32x3":
+        rh, rl = split_tf32(re)
+        ih, il = split_tf32(im)
         return s, [(rh, ih), (rl, il)]
     raise ValueError(prec)
 

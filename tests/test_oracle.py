@@ -398,6 +398,54 @@ def test_fp16_bits_cases():
     assert [int(g) for g in oracle.fp16_bits(x)] == [c[1] for c in FP16_CASES]
 
 
+# TF32 (8 exponent bits, 10 stored fraction bits): FP32 pattern -> rounded FP32 pattern
+TF32_CASES = [
+    (0x3F800000, 0x3F800000),  # 1.0 exact
+    (0x3F801000, 0x3F800000),  # 1 + 2^-11, halfway 1.0 / 1 + 2^-10 -> even (1.0)
+    (0x3F803000, 0x3F804000),  # 1 + 3*2^-11, halfway, odd kept part -> up to even
+    (0x3F801001, 0x3F802000),  # just above halfway -> up
+    (0x3F800FFF, 0x3F800000),  # just below halfway -> down
+    (0xBF801000, 0xBF800000),  # sign is kept
+    (0x3FFFF000, 0x40000000),  # 2 - 2^-11: halfway, odd -> carry into the exponent (2.0)
+    (0x00000000, 0x00000000),
+    (0x80000000, 0x80000000),
+]
+
+
+def test_tf32_round_to_nearest_even_cases():
+    x = np.array([c[0] for c in TF32_CASES], dtype=np.uint32).view(np.float32)
+    got = oracle.tf32_round(x).view(np.uint32)
+    assert [int(g) for g in got] == [c[1] for c in TF32_CASES]
+
+
+def test_tf32_round_is_the_nearest_tf32_value():
+    """Against the definition, in FP64: of the two TF32 values around x (x with
+    the 13 low bits cleared, and that plus one TF32 ulp), the nearer one, the
+    one with an even last kept bit on a tie."""
+    rng = np.random.default_rng(24)
+    x = np.concatenate([rng.normal(size=20000), rng.normal(size=2000) * 1e-30,
+                        rng.normal(size=2000) * 1e30, np.ldexp(1.0 + np.arange(64) * 2.0 ** -11, 3)])
+    x = x.astype(np.float32)
+    bits = x.view(np.uint32)
+    lo = (bits & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)  # toward zero
+    hi = ((bits & np.uint32(0xFFFFE000)) + np.uint32(0x2000)).view(np.float32).astype(np.float64)  # away
+    xd = x.astype(np.float64)
+    dlo, dhi = np.abs(xd - lo), np.abs(hi - xd)
+    even_lo = ((bits >> np.uint32(13)) & np.uint32(1)) == 0
+    want = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(even_lo, lo, hi)))
+    assert np.array_equal(oracle.tf32_round(x).astype(np.float64), want)
+
+
+def test_split_tf32_bound():
+    """hi + lo reproduces x to 2^-22 relative; both parts are TF32 values."""
+    rng = np.random.default_rng(25)
+    x = rng.normal(size=50000).astype(np.float32)
+    hi, lo = oracle.split_tf32(x)
+    assert np.array_equal(oracle.tf32_round(hi), hi) and np.array_equal(oracle.tf32_round(lo), lo)
+    err = np.abs(x.astype(np.float64) - hi.astype(np.float64) - lo.astype(np.float64))
+    assert np.all(err <= 2.0 ** -22 * np.abs(x.astype(np.float64)))
+
+
 def test_split_bf16_bound():
     """hi + lo reproduces x to 2^-16 relative; both parts are bf16 values."""
     rng = np.random.default_rng(23)
