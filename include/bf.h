@@ -147,6 +147,27 @@ bf_status bf_selftest_wait_timeout(bf_plan plan, int32_t *out_host);
 bf_status bf_set_precoders(bf_plan plan, const void *W_dev, const int32_t *f_host,
                            int32_t n_prec, int32_t first_id, void *stream);
 
+/* The images bf_set_precoders made of one precoder slot, copied to host
+ * memory (inspection and tests; synchronises the device):
+ *  BF_IMG_FP32   : FP32 planes for the CUDA-core kernels, float index k*64 + i
+ *                  of plane 0 = Re W[i][k], plane 1 = Im W[i][k], plane 2 =
+ *                  Re + Im (FP32 sum); 3 * 64 * f floats.
+ *  BF_IMG_BF16X2 : bf16 hi image then lo image of the real-block operand B
+ *                  (row n = 2i + c, column kk = 2k + c': row 2i = (Re, -Im),
+ *                  row 2i + 1 = (Im, Re), all divided by the slot's scale),
+ *                  K = 2f rounded up to 16, each in the layout of held S
+ *                  (bf_held_block_bytes) with 128 rows; 2 * 128 * K * 2 bytes.
+ *  BF_IMG_FP16   : the same operand in fp16; 128 * K * 2 bytes.
+ *  BF_IMG_TF32X2 : tf32 hi then lo image of the operand, K = 2f rounded up to
+ *                  8, 32-bit values at (row/8)*32*K + (col/4)*128 + (row%8)*16
+ *                  + (col%4)*4; 2 * 128 * K * 4 bytes.
+ *  BF_IMG_SCALE  : the slot's power-of-two scale, one float.
+ * With host_out NULL only *bytes_out is set. BF_ENOTFOUND for an unset slot,
+ * BF_EINVAL for an unknown kind or capacity < the image size. */
+typedef enum { BF_IMG_FP32 = 0, BF_IMG_BF16X2 = 1, BF_IMG_FP16 = 2, BF_IMG_TF32X2 = 3, BF_IMG_SCALE = 4 } bf_image;
+bf_status bf_get_precoder_image(bf_plan plan, int32_t slot, bf_image kind, void *host_out, int64_t capacity,
+                                int64_t *bytes_out);
+
 /* Grow the precoder store to at least n_slots slots now, so that later
  * bf_set_precoders calls on slots below n_slots never reallocate it (growing
  * synchronises the device and copies every image, which a latency-bound

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
             "bf_reserve_precoders": (c_int, [c_void_p, c_int32]),
             "bf_reserve_worklists": (c_int, [c_void_p, c_int64]),
+            "bf_get_precoder_image": (c_int, [c_void_p, c_int32, c_int, c_void_p, c_int64, POINTER(c_int64)]),
             "bf_held_block_bytes": (c_int64, [c_int, c_int]),
             "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
                                             POINTER(c_int64), c_void_p, c_void_p]),
@@ -208,6 +209,19 @@ def bf_selftest_wait_timeout(plan) -> dict:
 
 def bf_reserve_precoders(plan, n_slots: int) -> None:
     _check(lib().bf_reserve_precoders(plan, int(n_slots)), plan)
+
+
+BF_IMG_FP32, BF_IMG_BF16X2, BF_IMG_FP16, BF_IMG_TF32X2, BF_IMG_SCALE = range(5)
+
+
+def bf_get_precoder_image(plan, slot: int, kind: int):
+    """The slot's image of the given kind as a numpy uint8 array (host copy)."""
+    import numpy as np
+    n = c_int64()
+    _check(lib().bf_get_precoder_image(plan, int(slot), int(kind), None, 0, ctypes.byref(n)), plan)
+    out = np.zeros(max(1, n.value), dtype=np.uint8)
+    _check(lib().bf_get_precoder_image(plan, int(slot), int(kind), out.ctypes.data, n.value, ctypes.byref(n)), plan)
+    return out[:n.value]
 
 
 def bf_reserve_worklists(plan, max_blocks: int) -> None:

@@ -310,6 +310,49 @@ static bf_status ensure_slots(bf_plan plan, int need) {
     return BF_OK;
 }
 
+extern "C" bf_status bf_get_precoder_image(bf_plan plan, int32_t slot, bf_image kind, void *host_out,
+                                         int64_t capacity, int64_t *bytes_out) {
+    if (!plan || !bytes_out) return bf_fail(plan, BF_EINVAL, "NULL argument");
+    if (slot < 0 || slot >= plan->cap || plan->f_slot[slot] < 0)
+        return bf_fail(plan, BF_ENOTFOUND, "precoder slot %d is not set", slot);
+    const int f = plan->f_slot[slot];
+    const uint8_t *src = nullptr;
+    int64_t bytes = 0;
+    switch (kind) {
+        case BF_IMG_FP32:
+            src = plan->w_simt + (int64_t)slot * W_SIMT_STRIDE;
+            bytes = simt_img_bytes(f, 3);
+            break;
+        case BF_IMG_BF16X2:
+            src = plan->w_bf16x2 + (int64_t)slot * W_BF16X2_STRIDE;
+            bytes = 2 * (int64_t)tc_img_bytes(kpad_of(f));
+            break;
+        case BF_IMG_FP16:
+            src = plan->w_fp16 + (int64_t)slot * W_FP16_STRIDE;
+            bytes = tc_img_bytes(kpad_of(f));
+            break;
+        case BF_IMG_TF32X2:
+            src = plan->w_tf32x2 + (int64_t)slot * W_TF32X2_STRIDE;
+            bytes = 2 * (int64_t)tf32_img_bytes(kpad32_of(f));
+            break;
+        case BF_IMG_SCALE:
+            src = reinterpret_cast<const uint8_t *>(plan->w_scale + slot);
+            bytes = sizeof(float);
+            break;
+        default:
+            return bf_fail(plan, BF_EINVAL, "unknown image kind %d", (int)kind);
+    }
+    *bytes_out = bytes;
+    if (!host_out) return BF_OK;
+    if (capacity < bytes) return bf_fail(plan, BF_EINVAL, "capacity %lld < %lld bytes", (long long)capacity,
+                                         (long long)bytes);
+    bf_status s = plan_ensure_device(plan);
+    if (s != BF_OK) return s;
+    BF_CK(plan, cudaDeviceSynchronize());
+    BF_CK(plan, cudaMemcpy(host_out, src, (size_t)bytes, cudaMemcpyDeviceToHost));
+    return BF_OK;
+}
+
 extern "C" bf_status bf_reserve_worklists(bf_plan plan, int64_t max_blocks) {
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
     if (max_blocks < 0 || max_blocks > (int64_t)1 << 30) return bf_fail(plan, BF_EINVAL, "max_blocks out of range");
