@@ -156,6 +156,30 @@ def test_reduced_mechanics(plan, prec, name):
         assert e < 2e-6, f"{name}: group {g} mechanics error {e:.2e}"
 
 
+@pytest.mark.parametrize("prec,name", [(bf.BF_BF16X3, "bf16x3"), (bf.BF_TF32X3, "tf32x3"), (bf.BF_BF16, "bf16"),
+                                       (bf.BF_FP16, "fp16")])
+def test_onchip_mechanics(plan, prec, name):
+    """Complex64 S encoded on chip (no per-block scale; the precoder keeps its
+    power-of-two scale) against the FP64 product of the oracle's encodings of
+    the same operands: only FP32 accumulation rounding separates them, so a
+    wrong rounding, split or dropped term shows up far above the bound."""
+    batch = wl.config_reduced(seed=4, copies=1, n_rb=9, n_sym=5)
+    R = run(plan, batch, prec, torch)
+    split = name in ("bf16x3", "tf32x3")
+    for g, (p, S) in enumerate(zip(batch.prec, batch.S)):
+        W = batch.W[p].astype(np.complex64)
+        sw, wpl = oracle.quantize_planes(W, name)
+        Wt = [a + 1j * b for a, b in wpl]
+        pairs = [(0, 0), (0, 1), (1, 0)] if split else [(0, 0)]
+        exp = np.empty((S.shape[0], 64, 60), np.complex128)
+        for n in range(S.shape[0]):
+            _, spl = oracle.quantize_planes(S[n].astype(np.complex64), name, scaled=False)
+            St = [(a + 1j * b)[None] for a, b in spl]
+            exp[n] = oracle.apply_terms(Wt, St, pairs, sw)[0]
+        e = oracle.rel_frobenius([R[g]], [exp])
+        assert e < 2e-6, f"{name}: group {g} mechanics error {e:.2e}"
+
+
 def test_reduced_accuracy(plan):
     """The reduced-precision workload (256-QAM + noise, f = 36), scaled down."""
     batch = wl.config_reduced(seed=4, copies=1, n_rb=20, n_sym=14)
