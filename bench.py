@@ -502,6 +502,7 @@ def filter_leg(torch, bf, b, sample, stream, steps=100):
     f = bf.bf_filter_create(2048)
     h = to_device_c64(b.h, torch)
     bf.bf_filter_set_taps(f, h, len(b.h), stream)
+    bf.bf_filter_set_s_independent(f)  # S is filled once, by a copy; the filter never writes it
     S = to_device_c64(b.s, torch)
     Y = torch.empty_like(S)
     for _ in range(5):

@@ -332,6 +332,7 @@ def _filter_sigs(L):
             "bf_filter_apply": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
             "bf_filter_apply_host": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
             "bf_filter_launch_count": (c_int64, [c_void_p]),
+            "bf_filter_set_s_independent": (c_int, [c_void_p, c_int32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -375,6 +376,11 @@ def bf_filter_apply(filt, s_dev, n_sig: int, y_dev, stream=None) -> None:
 def bf_filter_apply_host(filt, s_host, n_sig: int, y_host, stream=None) -> None:
     _fcheck(_filter_sigs(lib()).bf_filter_apply_host(filt, _ptr(s_host), int(n_sig), _ptr(y_host), _stream(stream)),
             filt)
+
+
+def bf_filter_set_s_independent(filt, independent: bool = True) -> None:
+    """Declare that no pending filter launch writes the s of later calls (see bf_filter.h)."""
+    _fcheck(_filter_sigs(lib()).bf_filter_set_s_independent(filt, 1 if independent else 0), filt)
 
 
 def bf_filter_launch_count(filt) -> int:

@@ -267,10 +267,15 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
 }
 
 // FILTER: y = IFFT(Hs * FFT(s)) with Hs = FFT(h) / N; else y = FFT(s).
+// Filter launches use programmatic stream serialization: the prologue (the
+// twiddle table, written at creation, and the spectrum, written by a launch
+// without early release) runs while the previous launch on the stream
+// finishes; s is read only after that launch completes, unless s_indep says
+// that no pending filter launch writes it, and y is always written after it.
 template <bool FILTER>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     bf_filter_kernel(const float2 *s, float2 *y, long long n_sig, const float2 *__restrict__ tw_g,
-                     const float2 *__restrict__ H_g) {
+                     const float2 *__restrict__ H_g, int s_indep) {
     extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm;
     float2 *Hs = sm + TW_SIZE;
@@ -287,6 +292,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     __syncthreads();
     float2 w3[2][8];
     pass3_twiddles(w3, tw, t);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    bool dep_done = false;
+    if (!s_indep) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        dep_done = true;
+    }
     const long long stride = (long long)gridDim.x * TEAMS;
     long long q = (long long)blockIdx.x * TEAMS + team;
     if (PREFETCH && q < n_sig) prefetch_block(IN, s + q * N, t);
@@ -311,6 +322,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
             fft2048<1>(v, E, tw, w3, t, team);
         }
         float2 *yq = y + q * N;
+        if (!dep_done) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            dep_done = true;
+        }
 #pragma unroll
         for (int m = 0; m < 16; ++m) yq[t + 128 * m] = v[m];
     }
@@ -333,6 +348,7 @@ struct bf_filter_s {
     float2 *slot_s[3] = {}, *slot_y[3] = {};
     size_t slot_cap = 0;  // blocks per slot
     int slot_next = 0;    // next slot (the ring continues across calls)
+    bool s_indep = false; // bf_filter_set_s_independent
 };
 
 static thread_local std::string g_create_err;
@@ -363,16 +379,30 @@ static bf_status ff_device(bf_filter f) {
     return BF_OK;
 }
 
+// Filter launches may start while the previous kernel on the stream finishes
+// (see bf_filter_kernel); the spectrum launch releases its dependents only by
+// completing, so a filter launch never reads a spectrum still being written.
 static cudaError_t launch_filter(bool filter, const float2 *s, float2 *y, long long n_sig, const bf_filter f,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool s_indep = false) {
     if (n_sig <= 0) return cudaSuccess;
     const long long want = (n_sig + TEAMS - 1) / TEAMS;
     const int grid = (int)std::min<long long>(want, (long long)f->sm_count * CTAS_PER_SM);
-    if (filter)
-        bf_filter_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, f->H);
-    else
-        bf_filter_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, nullptr);
-    return cudaGetLastError();
+    if (!filter) {
+        bf_filter_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, nullptr, 0);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bf_filter_kernel<true>, s, y, n_sig, (const float2 *)f->tw, (const float2 *)f->H,
+                              s_indep ? 1 : 0);
 }
 
 extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
@@ -499,8 +529,15 @@ extern "C" bf_status bf_filter_apply(bf_filter f, const void *s_dev, int64_t n_s
     bf_status s = ff_check_apply(f, s_dev, n_sig, y_dev, true);
     if (s != BF_OK || n_sig == 0) return s;
     if ((s = ff_device(f)) != BF_OK) return s;
-    FF_CK(f, launch_filter(true, (const float2 *)s_dev, (float2 *)y_dev, n_sig, f, (cudaStream_t)stream));
+    FF_CK(f, launch_filter(true, (const float2 *)s_dev, (float2 *)y_dev, n_sig, f, (cudaStream_t)stream, f->s_indep));
     f->launches++;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_set_s_independent(bf_filter f, int32_t independent) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (independent != 0 && independent != 1) return ff_fail(f, BF_EINVAL, "independent must be 0 or 1");
+    f->s_indep = independent != 0;
     return BF_OK;
 }
 

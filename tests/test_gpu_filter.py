@@ -199,3 +199,34 @@ def test_host_path_pipelines_across_streams(filt):
     for k in range(2):
         streams[k].synchronize()
         assert torch.equal(y_h[k].view(torch.int32), want)
+
+
+def test_independent_input_keeps_the_y_side_ordered(filt):
+    """With s declared independent of pending filter launches, a call reads and
+    transforms s while the previous launch finishes but writes y only after
+    it: call B writes its y over the s that call A (launched just before) is
+    still reading. Over repeated pairs both outputs equal the same calls run
+    alone, bit for bit; the setter rejects values other than 0 and 1."""
+    b = wl.config_filter_tti().rounded()  # 896 blocks
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    sa = dev_c64(b.s).view(-1)
+    sb = dev_c64(b.s[::-1].copy()).view(-1)
+    ya_ref, yb_ref = torch.empty_like(sa), torch.empty_like(sb)
+    bf.bf_filter_apply(filt, sa, b.n_sig, ya_ref)
+    bf.bf_filter_apply(filt, sb, b.n_sig, yb_ref)
+    torch.cuda.synchronize()
+    big = torch.empty_like(sa)        # A reads its s here; B writes its y here
+    ya = torch.empty_like(sa)
+    bf.bf_filter_set_s_independent(filt, True)
+    try:
+        for rep in range(20):
+            big.copy_(sa)             # a copy, not a filter launch, writes A's s
+            ya.fill_(float("nan"))
+            bf.bf_filter_apply(filt, big, b.n_sig, ya)
+            bf.bf_filter_apply(filt, sb, b.n_sig, big)
+            torch.cuda.synchronize()
+            assert torch.equal(ya.view(torch.int32), ya_ref.view(torch.int32)), f"A, pair {rep}"
+            assert torch.equal(big.view(torch.int32), yb_ref.view(torch.int32)), f"B, pair {rep}"
+        assert bf.lib().bf_filter_set_s_independent(filt, 2) == bf.BF_EINVAL
+    finally:
+        bf.bf_filter_set_s_independent(filt, False)
