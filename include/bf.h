@@ -294,11 +294,13 @@ bf_status bf_batch_launch(bf_batch batch, void *stream);
 bf_status bf_batch_launch_graph(bf_batch batch, void *stream);
 bf_status bf_batch_destroy(bf_batch batch);
 
-/* Declare (independent = 1) that none of the product launches of this
- * library (bf_apply_batch*, bf_batch_launch*) enqueued on the stream since its
- * last other operation (a copy, another kernel, an event wait) writes this
- * batch's S or held-S scales -- as when S lives in its own buffers, filled by
- * copies or other kernels, in a double-buffered pipeline. bf_batch_launch then
+/* Declare (independent = 1) that none of the launches of this library
+ * (bf_apply_batch*, bf_batch_launch*, bf_filter_apply*) enqueued on the
+ * stream since its last other operation (a copy, another kernel, an event
+ * wait) writes this batch's S or held-S scales -- as when S lives in its own
+ * buffers, filled by copies or other kernels, in a double-buffered pipeline.
+ * (Those launches may release the next launch before they complete; other
+ * work does not.) bf_batch_launch then
  * loads S and computes while those launches finish; only its stores of R wait
  * for them (R may overlap what they read or write). A wrong declaration gives
  * wrong results. Default 0. The captured graph (bf_batch_launch_graph) keeps

@@ -72,10 +72,11 @@ bf_status bf_filter_apply(bf_filter filter, const void *s_dev, int64_t n_sig, vo
 bf_status bf_filter_apply_host(bf_filter filter, const void *s_host, int64_t n_sig, void *y_host,
                                void *stream);
 
-/* Declare (independent = 1) that none of the filter launches enqueued on the
- * stream since its last other operation (a copy, another kernel, an event
- * wait) writes the s of the following bf_filter_apply calls -- as when the
- * signals are filled by copies, not filtered in place by those launches. A
+/* Declare (independent = 1) that none of the launches of this library
+ * (bf_filter_apply*, bf_apply_batch*, bf_batch_launch*) enqueued on the stream
+ * since its last other operation (a copy, another kernel, an event wait)
+ * writes the s of the following bf_filter_apply calls -- as when the signals
+ * are filled by copies, not filtered in place by those launches. A
  * call then reads and transforms s while the previous launch finishes; its
  * stores of y still wait for it. A wrong declaration gives wrong results.
  * Default 0 (s is read after the previous launch completes). The host-buffer

@@ -91,9 +91,9 @@ struct KParams {
     int64_t r_block_stride;
     int32_t r_type;
     int32_t r_esize;
-    // 1: no product launch enqueued since the stream's last other operation
-    // writes S or s_scale, so the kernel reads S before the previous grid on
-    // the stream completes (only its stores of R wait)
+    // 1: no launch of this library (product or filter) enqueued since the
+    // stream's last other operation writes S or s_scale, so the kernel reads S
+    // before the previous grid on the stream completes (only its R stores wait)
     int32_t s_independent;
     int32_t reserved;
 };
