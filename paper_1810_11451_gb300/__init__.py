@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "bf_set_precoders": (c_int, [c_void_p, c_void_p, POINTER(c_int32), c_int32, c_int32, c_void_p]),
             "bf_reserve_precoders": (c_int, [c_void_p, c_int32]),
             "bf_reserve_worklists": (c_int, [c_void_p, c_int64]),
+            "bf_set_host_chunks": (c_int, [c_void_p, c_int64, c_int64]),
             "bf_get_precoder_image": (c_int, [c_void_p, c_int32, c_int, c_void_p, c_int64, POINTER(c_int64)]),
             "bf_held_block_bytes": (c_int64, [c_int, c_int]),
             "bf_quantize_symbols": (c_int, [c_void_p, c_void_p, POINTER(bf_group), c_int32, c_int, c_void_p,
@@ -222,6 +223,10 @@ def bf_get_precoder_image(plan, slot: int, kind: int):
     out = np.zeros(max(1, n.value), dtype=np.uint8)
     _check(lib().bf_get_precoder_image(plan, int(slot), int(kind), out.ctypes.data, n.value, ctypes.byref(n)), plan)
     return out[:n.value]
+
+
+def bf_set_host_chunks(plan, first_bytes: int, max_bytes: int) -> None:
+    _check(lib().bf_set_host_chunks(plan, int(first_bytes), int(max_bytes)), plan)
 
 
 def bf_reserve_worklists(plan, max_blocks: int) -> None:

@@ -353,6 +353,15 @@ extern "C" bf_status bf_get_precoder_image(bf_plan plan, int32_t slot, bf_image 
     return BF_OK;
 }
 
+extern "C" bf_status bf_set_host_chunks(bf_plan plan, int64_t first_bytes, int64_t max_bytes) {
+    if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
+    if (first_bytes < (1 << 16) || max_bytes < first_bytes || max_bytes > ((int64_t)1 << 34))
+        return bf_fail(plan, BF_EINVAL, "chunk sizes must satisfy 64 KiB <= first <= max <= 16 GiB");
+    plan->host_chunk_first = first_bytes;
+    plan->host_chunk_bytes = max_bytes;
+    return BF_OK;
+}
+
 extern "C" bf_status bf_reserve_worklists(bf_plan plan, int64_t max_blocks) {
     if (!plan) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
     if (max_blocks < 0 || max_blocks > (int64_t)1 << 30) return bf_fail(plan, BF_EINVAL, "max_blocks out of range");
@@ -861,7 +870,7 @@ extern "C" bf_status bf_apply_batch_host(bf_plan plan, const void *S_host, const
     // copy-out starts early, later ones double up to host_chunk_bytes (large
     // enough that issuing a chunk's calls takes less host time than the link
     // takes to move it)
-    int64_t target = std::min<int64_t>(BF_HOST_CHUNK_FIRST, plan->host_chunk_bytes);
+    int64_t target = std::min<int64_t>(plan->host_chunk_first, plan->host_chunk_bytes);
     std::vector<int> cut{0};
     int64_t acc = 0, max_s = 0, max_r = 0, cs = 0, cr = 0;
     for (int g = 0; g < n_groups; ++g) {

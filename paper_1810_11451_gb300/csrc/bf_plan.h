@@ -82,7 +82,7 @@ struct StageBuf {
 #define BF_HOST_CHUNK_BYTES (32 << 20)
 #endif
 #ifndef BF_HOST_CHUNK_FIRST
-#define BF_HOST_CHUNK_FIRST (2 << 20)
+#define BF_HOST_CHUNK_FIRST (4 << 20)
 #endif
 
 struct bf_plan_s {
@@ -121,7 +121,7 @@ struct bf_plan_s {
     uint8_t *x_s[BF_XFER_SLOTS] = {}, *x_r[BF_XFER_SLOTS] = {};
     size_t x_scap[BF_XFER_SLOTS] = {}, x_rcap[BF_XFER_SLOTS] = {};
     int x_next = 0;  // next staging slot (the ring continues across calls)
-    int64_t host_chunk_bytes = BF_HOST_CHUNK_BYTES;
+    int64_t host_chunk_first = BF_HOST_CHUNK_FIRST, host_chunk_bytes = BF_HOST_CHUNK_BYTES;
     // tuning and counters
     bfi::TuneTable tune;
     int64_t launches = 0;

@@ -426,6 +426,21 @@ def test_host_path_pipelines_across_streams(plan):
         streams[k].synchronize()
         got = R_h[k].numpy().view(np.complex64).reshape(-1, 64, 60)
         assert np.array_equal(got.view(np.uint64), np.concatenate(ref).view(np.uint64))
+    # other chunk sizes move the same bits
+    try:
+        for first, mx in ((64 << 10, 1 << 20), (8 << 20, 64 << 20)):
+            bf.bf_set_host_chunks(plan, first, mx)
+            R_h[0].fill_(float("nan"))
+            bf.bf_apply_batch_host(plan, S_h[0], lay.groups, bf.BF_BF16X3, R_h[0], streams[0])
+            streams[0].synchronize()
+            got = R_h[0].numpy().view(np.complex64).reshape(-1, 64, 60)
+            assert np.array_equal(got.view(np.uint64), np.concatenate(ref).view(np.uint64)), (first, mx)
+        for first, mx in ((1 << 10, 1 << 20), (8 << 20, 4 << 20)):
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_set_host_chunks(plan, first, mx)
+            assert ei.value.status == bf.BF_EINVAL
+    finally:
+        bf.bf_set_host_chunks(plan, 4 << 20, 32 << 20)
 
 
 @pytest.mark.parametrize("prec", [bf.BF_BF16X3, bf.BF_TF32X3, bf.BF_FP32], ids=["bf16x3", "tf32x3", "fp32"])
