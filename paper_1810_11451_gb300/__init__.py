@@ -242,10 +242,22 @@ def bf_held_block_bytes(f: int, prec: int) -> int:
     return int(lib().bf_held_block_bytes(int(f), int(prec)))
 
 
+def make_offsets(q_off) -> ctypes.Array:
+    """ctypes int64 array of per-group byte offsets (built through numpy; an
+    existing c_int64 array passes through)."""
+    if isinstance(q_off, ctypes.Array) and q_off._type_ is c_int64:
+        return q_off
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(q_off, dtype=np.int64).reshape(-1))
+    if a.size == 0:
+        a = np.zeros(1, np.int64)
+    return (c_int64 * a.size).from_buffer(a.copy())
+
+
 def bf_quantize_symbols(plan, S_dev, groups, prec: int, Sq_dev, q_off: Sequence[int], scale_dev,
                         stream=None) -> None:
     ga, n = make_groups(groups)
-    qa = (c_int64 * max(1, len(q_off)))(*[int(q) for q in q_off])
+    qa = make_offsets(q_off)
     _check(lib().bf_quantize_symbols(plan, _ptr(S_dev), ga, n, int(prec), _ptr(Sq_dev), qa, _ptr(scale_dev),
                                      _stream(stream)), plan)
 
