@@ -35,9 +35,9 @@
 //   warp 2        bulk-loads each precoder image once per run of tiles
 //   warps 4..7    (complex64 input) convert raw S into the operand ring
 //   warps 8..11   epilogue: tensor memory -> registers -> global R
-// Tensor memory holds four 128-column accumulators (two for tf32, whose hi
-// operand stages take the other 256 columns) so the MMAs of later tiles
-// overlap the epilogue of earlier ones.
+// Tensor memory holds two or four 128-column accumulators (two for tf32,
+// whose hi operand stages take the other 256 columns) so the MMAs of later
+// tiles overlap the epilogue of earlier ones.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -61,11 +61,19 @@ static_assert(TC_CONV_WARPS % 4 == 0 && TC_EPI_WARPS % 4 == 0 && TC_EPI_WARPS <=
 constexpr int TC_CONV0 = 4;                          // first converter warp
 constexpr int TC_EPI0 = TC_CONV0 + TC_CONV_WARPS;    // first epilogue warp (a multiple of 4)
 constexpr int TC_THREADS = 32 * (TC_EPI0 + TC_EPI_WARPS);
+// Accumulators in tensor memory (2 or 4: a power-of-two allocation). The
+// split form on complex64 S measured faster with 2 (back to back over the
+// full band, 31.4 against 31.8 us), the single-pass and held forms with 4.
 #ifndef BF_TC_NACC
 #define BF_TC_NACC 4
 #endif
-constexpr int TC_NACC = BF_TC_NACC;  // accumulators in tensor memory (2 or 4: a power-of-two allocation)
-static_assert(TC_NACC == 2 || TC_NACC == 4, "tensor-memory allocation is a power of two columns");
+#ifndef BF_TC_SPLIT_C64_NACC
+#define BF_TC_SPLIT_C64_NACC 2
+#endif
+constexpr int TC_NACC = BF_TC_NACC;
+constexpr int TC_SPLIT_C64_NACC = BF_TC_SPLIT_C64_NACC;
+static_assert((TC_NACC == 2 || TC_NACC == 4) && (TC_SPLIT_C64_NACC == 2 || TC_SPLIT_C64_NACC == 4),
+              "tensor-memory allocation is a power of two columns");
 constexpr int TC_ACC_COLS = 128; // N
 constexpr int TC_RAW_SLOT = F_LIMIT * S_BYTES_PER_F;  // one complex64 block, 17,280 B
 constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shared memory per CTA
@@ -123,7 +131,7 @@ struct TcCfg {
     static constexpr int NR = HELD ? 0 : ST.nr;
     // tf32: the hi term of each operand stage lives in tensor memory
     static constexpr bool A_TMEM = OPK == OP_TF32;
-    static constexpr int NACC = A_TMEM ? 2 : TC_NACC;  // accumulators
+    static constexpr int NACC = A_TMEM ? 2 : (TERMS == 3 && !HELD ? TC_SPLIT_C64_NACC : TC_NACC);  // accumulators
     static constexpr int TMEM_A0 = NACC * TC_ACC_COLS; // first column of the hi stages (128 apart)
     static constexpr int TMEM_COLS = A_TMEM ? 512 : NACC * TC_ACC_COLS;
     static_assert(!A_TMEM || TMEM_A0 + 128 * (NA - 1) + 72 <= 512, "tensor-memory columns");
