@@ -672,6 +672,29 @@ def main():
     value = world * flops * args.steps / (total_ms * 1e-3) / 1e9
     blocks_s = world * batch.total_blocks * args.steps / (total_ms * 1e-3)
 
+    # ---- context for the roofline: a plain device copy moving the launch's
+    # algorithmic bytes (half read, half written) over the same number of
+    # rotating buffer sets, back to back. At this size the fixed cost of a
+    # launch keeps even a copy below the peak measured on large buffers.
+    copy_us = float("nan")
+    if not args.no_plain:
+        half = (alg_bytes // 2) // 16 * 4
+        srcs = [torch.zeros(half, dtype=torch.float32, device="cuda") for _ in range(n_sets)]
+        dsts = [torch.empty_like(srcs[0]) for _ in range(n_sets)]
+        for i in range(max(3, args.warmup)):
+            dsts[i % n_sets].copy_(srcs[i % n_sets])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k_copy = 300
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(k_copy):
+            dsts[i % n_sets].copy_(srcs[i % n_sets])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        copy_us = e0.elapsed_time(e1) * 1e3 / k_copy
+        copy_bytes = 2 * half * 4
+        del srcs, dsts
+
     # ---- the plain FP32 form on the same GPU
     k2 = max(50, args.steps // 10)
     p_ms = p3_ms = t32_ms = float("nan")
@@ -763,7 +786,12 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_for("bf_tc.cu"),
                      "peak_source": f"{peak_kind} hbm_gbs", "kernel": "bf_tc_kernel<3,false,OP_BF16>",
-                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes},
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes,
+                     "same_bytes_copy": None if copy_us != copy_us else {
+                         "us": copy_us, "gbs": copy_bytes / (copy_us * 1e3),
+                         "kernel_time_over_copy_time": kern_ms * 1e3 / copy_us,
+                         "how": f"torch copy_ of {copy_bytes / 2e6:.1f} MB into {copy_bytes / 2e6:.1f} MB, "
+                                f"{n_sets} rotating sets, back to back (context, not the peak)"}},
         "e2e": e2e,
         "cpu_baseline": cpu,
         "accuracy_rel_frobenius": acc,
