@@ -396,7 +396,7 @@ def bf_filter_apply_host(filt, s_host, n_sig: int, y_host, stream=None) -> None:
 
 
 def bf_filter_set_s_independent(filt, independent: bool = True) -> None:
-    """Declare that no pending filter launch writes the s of later calls (see bf_filter.h)."""
+    """Declare that no pending launch of the library writes the s of later calls (see bf_filter.h)."""
     _fcheck(_filter_sigs(lib()).bf_filter_set_s_independent(filt, 1 if independent else 0), filt)
 
 

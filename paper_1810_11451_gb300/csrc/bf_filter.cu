@@ -7,7 +7,8 @@
 // x[j + m N/R] of butterfly j, multiplies them by e^{-+2 pi i m k / (Ns R)},
 // k = j mod Ns, takes their R-point DFT and writes them to
 // (j div Ns) Ns R + k + q Ns (Ns = 1, 16, 256). The first pass reads the
-// block straight from global memory; between passes the values go through a
+// block from a shared-memory staging buffer that cp.async filled while the
+// team transformed its previous block; between passes the values go through a
 // padded shared-memory buffer (one pad word per 16 values keeps every access
 // free of bank conflicts); the last forward pass leaves in thread t exactly
 // the values X[t + 128 m], which is also what the first inverse pass needs,
@@ -271,7 +272,8 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
 // twiddle table, written at creation, and the spectrum, written by a launch
 // without early release) runs while the previous launch on the stream
 // finishes; s is read only after that launch completes, unless s_indep says
-// that no pending filter launch writes it, and y is always written after it.
+// that no pending launch of the library writes it, and y is always written
+// after it.
 template <bool FILTER>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     bf_filter_kernel(const float2 *s, float2 *y, long long n_sig, const float2 *__restrict__ tw_g,
