@@ -80,9 +80,11 @@ constexpr int SMEM_LIMIT = 232448;                     // 227 KB of dynamic shar
 
 // Ring depths per form as three digits: W buffers, operand stages (tiles),
 // raw complex64 slots (blocks). Chosen by measurement; each may be
-// overridden at compile time (e.g. -DBF_TC_SPLIT_C64_STAGES=223).
+// overridden at compile time (e.g. -DBF_TC_SPLIT_C64_STAGES=124). The split
+// form on complex64 S double-buffers W (its next precoder loads while the
+// current one is in use) at the price of a raw slot.
 #ifndef BF_TC_SPLIT_C64_STAGES
-#define BF_TC_SPLIT_C64_STAGES 124
+#define BF_TC_SPLIT_C64_STAGES 223
 #endif
 #ifndef BF_TC_SPLIT_HELD_STAGES
 #define BF_TC_SPLIT_HELD_STAGES 120
