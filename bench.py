@@ -384,8 +384,19 @@ def reduced_leg(torch, bf, plan, batch, ref_d, stream, steps=50):
             s_bytes = lay.s_bytes
         ms = graph_rate(torch, bf, h, steps, stream)
         bf.bf_batch_launch(h, stream)
+        # algorithmic bytes: unpadded S at the operand's type (240 f per block
+        # for one bf16/fp16 term, 480 f for two terms or complex64), W at the
+        # operand's type (256 f per precoder per 16-bit term, 512 f complex64),
+        # R complex64; the padded image bytes (K to a multiple of 16, b to 64)
+        # are only traffic
+        terms = 2 if prec == bf.BF_BF16X3 else 1
+        f = 36
+        alg = nb * ((240 * terms if held else 480) * f + 30720) + len(batch.W) * (256 * terms if held else 512) * f
+        peak, _ = peaks()
         r.update({"kernel_ms": ms, "gflops": batch.flops() / ms / 1e6, "blocks_per_s": nb / ms * 1e3,
+                  "moved_bytes": int(s_bytes + nb * 30720 + len(batch.W) * 64 * 36 * 8),
                   "moved_gbs": (s_bytes + nb * 30720 + len(batch.W) * 64 * 36 * 8) / ms / 1e6,
+                  "alg_bytes": int(alg), "alg_gbs": alg / ms / 1e6, "alg_frac": alg / ms / 1e6 / peak,
                   "rel_err": rel_err(torch, bf, plan, R, ref_d, nb, stream)})
         bf.bf_batch_destroy(h)
         if held:
@@ -704,6 +715,15 @@ def main():
         p3_ms = time_launches(torch, bf, [plain3[s] for s in range(n_sets)], k2, args.warmup, stream) / k2
         t32_ms = time_launches(torch, bf, [tf32[s] for s in range(n_sets)], k2, args.warmup, stream) / k2
 
+    # ---- the FP32 FMA rate of the CUDA cores: the plain form's roofline
+    fma = None
+    if not args.no_plain:
+        with ClockSampler(local) as fclk:
+            fma_tf, fma_ms = bf.bf_measure_fp32_peak(20000, 5, stream)
+        fma = {"tflops": fma_tf, "ms_per_launch": fma_ms, "clocks": fclk.summary(),
+               "how": "bf_measure_fp32_peak: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
+                      "best of 5 launches (CUDA events)"}
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -761,7 +781,7 @@ def main():
         run_leg(legs, "filter", filter_leg, torch, bf, b_filter, filter_sample, stream)
     if extra and "serving" in want:
         run_leg(legs, "serving_bf16x3", serving_leg, torch, bf, args.serving_ttis, bf.BF_BF16X3)
-        run_leg(legs, "serving_fp32", serving_leg, torch, bf, max(200, args.serving_ttis // 10), bf.BF_FP32)
+        run_leg(legs, "serving_fp32", serving_leg, torch, bf, args.serving_ttis, bf.BF_FP32)
     status = bf.bf_device_status(plan)
 
     peak, peak_kind = peaks()
@@ -776,7 +796,11 @@ def main():
         "blocks_per_s": blocks_s,
         "fp32_plain": {"value": world * flops / (p_ms * 1e-3) / 1e9 if p_ms == p_ms else None, "unit": UNIT, "ms_per_step": p_ms,
                        "kernel_ms": p_ms,
-                       "blocks_per_s": world * batch.total_blocks / (p_ms * 1e-3)},
+                       "blocks_per_s": world * batch.total_blocks / (p_ms * 1e-3),
+                       "roofline": None if fma is None or p_ms != p_ms else {
+                           "bound": "fma", "achieved_tflops": flops / (p_ms * 1e-3) / 1e12,
+                           "peak_tflops": fma["tflops"], "frac": flops / (p_ms * 1e-3) / 1e12 / fma["tflops"],
+                           "peak": fma}},
         "fp32_3m": {"value": world * flops / (p3_ms * 1e-3) / 1e9 if p3_ms == p3_ms else None, "unit": UNIT,
                     "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add"},
         "tf32x3": {"value": world * flops / (t32_ms * 1e-3) / 1e9 if t32_ms == t32_ms else None, "unit": UNIT,

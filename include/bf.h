@@ -369,10 +369,20 @@ bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream);
 bf_status bf_tune_query(bf_plan plan, bf_precision prec, int32_t f, double *ns_per_block,
                         int32_t *tile_blocks, int32_t *tuned);
 
-/* Write / read the plan's autotune table as JSON ("libbf-tune-1"). A table
- * is only meaningful on the kind of GPU that measured it. */
+/* Write / read the plan's autotune table as JSON ("libbf-tune-2"). The
+ * building blocks are chosen per size and target (Sec. IV), so a table records
+ * the target it was measured on: the device name, the compute capability
+ * (major * 10 + minor) and the SM count. bf_tune_load refuses, with BF_EINVAL
+ * and the reason in bf_last_error(plan), a table measured on another target,
+ * a table without a target, and any unreadable table; the plan's table is
+ * then unchanged. */
 bf_status bf_tune_save(bf_plan plan, const char *path);
 bf_status bf_tune_load(bf_plan plan, const char *path);
+
+/* The target check of bf_tune_load on its own, with no plan and no CUDA call:
+ * BF_OK when the table at `path` was measured on (device_name, cc, sm_count),
+ * BF_EINVAL otherwise (reason in bf_last_error(NULL)). */
+bf_status bf_tune_check_target(const char *path, const char *device_name, int32_t cc, int32_t sm_count);
 
 /* Accuracy targets of bf_select_form, from the accuracy classes of the
  * reduced-precision study: BF_TARGET_FP32 (relative Frobenius error <= 1e-5)
@@ -415,14 +425,29 @@ bf_status bf_errnorm(bf_plan plan, const void *R_dev, const void *Rref_dev, int6
  * the process exits.
  *  R_dev, Rref_dev, n_blocks, total_host : as bf_errnorm (no per-block output).
  * n_blocks above the maximum gives BF_EINVAL (text in bf_last_error(NULL)).
- * The first call on a device looks the array's device address up for that
- * device (the current one); make that first call before any stream capture.
+ * Every call looks the array's device address up for the current device and
+ * context (so a cudaDeviceReset or a change of context between calls is
+ * safe); the first lookup on a device may load the library's device code, so
+ * make the first call on each device before any stream capture.
  * All calls share the one array: calls whose kernels overlap on the GPU (on
  * different streams or host threads) race and may return wrong totals, so
  * order them. Synchronises `stream`. */
 #define BF_ERRNORM_NOALLOC_MAX_BLOCKS 65536
 bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev, int64_t n_blocks,
                              double *total_host, void *stream);
+
+/* ------------------------------------------------------------------ measurement */
+
+/* The FP32 fused multiply-add rate of the CUDA cores of the current device,
+ * the roofline denominator of the plain FP32 form: at f = 36 that form does
+ * 22.4 flop per algorithmic byte, above the CUDA-core ridge, so its bound is
+ * FMA issue (Sec. III: the paper's improved kernel is built on FMA). One
+ * kernel of 4 CTAs of 256 threads per SM runs 8 independent chains of
+ * 4 * iters FMAs per thread; after one warm-up launch, the best of `reps`
+ * launches timed with CUDA events on `stream` gives *tflops_host (2 flop per
+ * FMA) and *ms_host (may be NULL). iters in [1, 2^24], reps in [1, 1000],
+ * else BF_EINVAL. Synchronises `stream`. */
+bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *tflops_host, double *ms_host, void *stream);
 
 /* Number of product kernels (or graph replays) this plan has launched so far
  * (0 for a NULL plan). */

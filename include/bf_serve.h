@@ -44,6 +44,13 @@ typedef struct {
                                   admission, batching and failure paths on machines
                                   without a GPU); the plan argument may then be NULL      */
     int64_t hbm_budget_bytes;  /* admission budget (> 0)                                   */
+    int32_t deadline_us;       /* per-job latency deadline for the statistics (>= 0; 0: the
+                                  0.5 ms TTI of Sec. II's slot timing, 500 us)              */
+    int32_t slot_timeout_us;   /* watchdog (>= 0; 0: 50,000 us): a launch whose completion is
+                                  not seen this long after it was enqueued fails its jobs
+                                  with BF_ETIMEOUT (see bf_poll); its slot and the jobs'
+                                  budget stay held until the launch does complete, since the
+                                  device may still be writing their R                      */
 } bf_serve_config;
 
 typedef struct {
@@ -65,6 +72,17 @@ typedef struct {
     int64_t max_inflight_bytes;
     int32_t max_busy_slots;    /* most launches seen in flight together                    */
     int32_t max_jobs_per_launch;
+    int64_t over_deadline;     /* jobs completed (or timed out) later than the deadline     */
+    int64_t timed_out;         /* jobs failed by the watchdog with BF_ETIMEOUT               */
+    int64_t deadline_ns, slot_timeout_ns;  /* the limits in use                            */
+    /* The job with the largest latency so far, and where its time went:
+     * submit = arrival -> bf_submit called (a late caller), queue = bf_submit ->
+     * admitted by the dispatcher (budget, free slot, FIFO), launch = admitted ->
+     * launch enqueued (host side: waits on precoder conversions, scheduling,
+     * the launch call), device = enqueued -> completion seen by the dispatcher. */
+    int64_t worst_latency_ns, worst_submit_ns, worst_queue_ns, worst_launch_ns, worst_device_ns;
+    /* Over-deadline jobs by the largest of those four parts of their latency. */
+    int64_t over_by_submit, over_by_queue, over_by_launch, over_by_device;
 } bf_serve_stats;
 
 /* Monotonic clock (CLOCK_MONOTONIC) in nanoseconds, the clock of arrival_ns. */
@@ -91,11 +109,16 @@ bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticket);
 
 /* Non-blocking completion check. *done = 1 when the job has finished; then
  * *latency_us (if not NULL) is completion minus arrival, and the ticket is
- * retired (a later poll gives BF_ENOTFOUND). BF_ENOTFOUND for unknown tickets. */
+ * retired (a later poll gives BF_ENOTFOUND). The return value is then the
+ * job's own status: BF_OK, BF_ECUDA for a failed launch, or BF_ETIMEOUT when
+ * the watchdog gave its launch up (slot_timeout_us; its R must not be used).
+ * BF_ENOTFOUND for unknown tickets. */
 bf_status bf_poll(bf_server srv, uint64_t ticket, int *done, double *latency_us);
 
 /* Block until the job is done or `timeout_us` passes (BF_ETIMEOUT; the job
- * stays queued or running). Retires the ticket on success like bf_poll. */
+ * stays queued or running and its ticket stays valid). Once the job is done it
+ * retires the ticket and returns the job's status like bf_poll (BF_ETIMEOUT
+ * there means the watchdog gave the launch up; the ticket is then retired). */
 bf_status bf_wait(bf_server srv, uint64_t ticket, int64_t timeout_us, double *latency_us);
 
 /* Hold (1) or resume (0) admission of queued jobs; jobs in flight continue.

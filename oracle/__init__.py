@@ -11,7 +11,8 @@ Contents
   * `rel_frobenius`, `errnorm_blocks`: the accuracy report -- sum |R - Rref|^2
     and sum |Rref|^2 per block and in total, relative Frobenius error.
   * `bf16_round`, `fp16_round`, `tf32_round`, `split_bf16`, `split_tf32`,
-    `pow2_scale`, `quantize_planes`: the reduced-precision operand encodings
+    `pow2_scale`, `quantize_planes`, `quantize_blocks`: the reduced-precision
+    operand encodings
     (the paper fixes no data type; the readings are: round to nearest even, a
     power-of-two per-block scale taken from the component-wise max-abs, split
     x = hi + lo with hi = round(x) and lo = round(x - hi), all decided in FP32
@@ -206,15 +207,19 @@ def split_bf16(x: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     return hi, lo
 
 
+def pow2_scales(maxabs: np.ndarray) -> np.ndarray:
+    """pow2_scale of every element of an array of FP32 max-abs values."""
+    m = np.asarray(maxabs, dtype=np.float32)
+    mant, ex = np.frexp(m)          # m = mant * 2^ex, mant in [0.5, 1)
+    e = np.where(mant == 0.5, ex - 1, ex)
+    s = np.ldexp(np.float32(1.0), e).astype(np.float64)
+    return np.where(m == 0, 1.0, s)
+
+
 def pow2_scale(maxabs: float) -> float:
     """The power of two 2^e with e = ceil(log2(maxabs)), so maxabs / 2^e is in
     (1/2, 1]; 1.0 when maxabs is 0. Decided exactly from the FP32 value."""
-    m = np.float32(maxabs)
-    if m == 0:
-        return 1.0
-    mant, ex = np.frexp(m)          # m = mant * 2^ex, mant in [0.5, 1)
-    e = int(ex) - 1 if mant == 0.5 else int(ex)
-    return float(np.ldexp(np.float32(1.0), e))
+    return float(pow2_scales(np.array([maxabs]))[0])
 
 
 def block_maxabs(x: np.ndarray) -> float:
@@ -223,6 +228,23 @@ def block_maxabs(x: np.ndarray) -> float:
     if x.size == 0:
         return 0.0
     return float(max(np.max(np.abs(x.real)), np.max(np.abs(x.imag))))
+
+
+def _encode(re: np.ndarray, im: np.ndarray, prec: str):
+    """The planes of already scaled FP32 parts (round to nearest even)."""
+    if prec == "bf16":
+        return [(bf16_round(re), bf16_round(im))]
+    if prec == "fp16":
+        return [(fp16_round(re), fp16_round(im))]
+    if prec == "bf16x3":
+        rh, rl = split_bf16(re)
+        ih, il = split_bf16(im)
+        return [(rh, ih), (rl, il)]
+    if prec == "tf32x3":
+        rh, rl = split_tf32(re)
+        ih, il = split_tf32(im)
+        return [(rh, ih), (rl, il)]
+    raise ValueError(prec)
 
 
 def quantize_planes(x: np.ndarray, prec: str, scaled: bool = True):
@@ -237,19 +259,26 @@ def quantize_planes(x: np.ndarray, prec: str, scaled: bool = True):
     inv = np.float32(1.0 / s)
     re = (x.real.astype(np.float32) * inv).astype(np.float32)
     im = (x.imag.astype(np.float32) * inv).astype(np.float32)
-    if prec == "bf16":
-        return s, [(bf16_round(re), bf16_round(im))]
-    if prec == "fp16":
-        return s, [(fp16_round(re), fp16_round(im))]
-    if prec == "bf16x3":
-        rh, rl = split_bf16(re)
-        ih, il = split_bf16(im)
-        return s, [(rh, ih), (rl, il)]
-    if prec == "tf32x3":
-        rh, rl = split_tf32(re)
-        ih, il = split_tf32(im)
-        return s, [(rh, ih), (rl, il)]
-    raise ValueError(prec)
+    return s, _encode(re, im, prec)
+
+
+def quantize_blocks(S: np.ndarray, prec: str, scaled: bool = True):
+    """quantize_planes applied to every block of S (n_blocks, f, b) at once:
+    the same steps (component-wise max-abs per block, its power-of-two scale,
+    the FP32 product with the scale's inverse, the encoding), vectorised over
+    blocks. Returns (scales (n_blocks,) float64, planes as (re, im) pairs of
+    (n_blocks, f, b) float32 arrays)."""
+    S = np.asarray(S, dtype=np.complex64)
+    n = S.shape[0]
+    if scaled and S[0].size:
+        m = np.maximum(np.abs(S.real).reshape(n, -1).max(axis=1), np.abs(S.imag).reshape(n, -1).max(axis=1))
+        s = pow2_scales(m)
+    else:
+        s = np.ones(n)
+    inv = (1.0 / s).astype(np.float32).reshape((n,) + (1,) * (S.ndim - 1))
+    re = (S.real.astype(np.float32) * inv).astype(np.float32)
+    im = (S.imag.astype(np.float32) * inv).astype(np.float32)
+    return s, _encode(re, im, prec)
 
 
 def apply_terms(W_terms, S_terms, pairs, scale: float = 1.0, _lib=None) -> np.ndarray:

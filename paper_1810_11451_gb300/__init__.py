@@ -456,6 +456,14 @@ def bf_tune_load(plan, path: str) -> None:
     _check(_tune_sigs(lib()).bf_tune_load(plan, path.encode()), plan)
 
 
+def bf_tune_check_target(path: str, device_name: str, cc: int, sm_count: int) -> None:
+    """Raises BfError (BF_EINVAL) unless the table at path was measured on this target."""
+    L = lib()
+    L.bf_tune_check_target.restype = c_int
+    L.bf_tune_check_target.argtypes = [ctypes.c_char_p, ctypes.c_char_p, c_int32, c_int32]
+    _check(L.bf_tune_check_target(path.encode(), device_name.encode(), int(cc), int(sm_count)))
+
+
 BF_ERRNORM_NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -472,10 +480,23 @@ def bf_errnorm_noalloc(R_dev, Rref_dev, n_blocks: int, stream=None) -> Tuple[flo
     return float(tot[0]), float(tot[1])
 
 
+def bf_measure_fp32_peak(iters: int = 20000, reps: int = 5, stream=None) -> Tuple[float, float]:
+    """(TFLOP/s, ms per launch) of the CUDA cores' FP32 FMA probe."""
+    L = lib()
+    L.bf_measure_fp32_peak.restype = c_int
+    L.bf_measure_fp32_peak.argtypes = [c_int32, c_int32, POINTER(c_double), POINTER(c_double), c_void_p]
+    t, ms = c_double(), c_double()
+    st = L.bf_measure_fp32_peak(int(iters), int(reps), ctypes.byref(t), ctypes.byref(ms), _stream(stream))
+    if st != BF_OK:
+        raise BfError(st, bf_last_error(None))
+    return float(t.value), float(ms.value)
+
+
 # ---------------------------------------------------------------- serving (bf_serve.h)
 class bf_serve_config(ctypes.Structure):
     _fields_ = [("n_slots", c_int32), ("max_batch_jobs", c_int32), ("queue_capacity", c_int32),
-                ("fake_device_us", c_int32), ("hbm_budget_bytes", c_int64)]
+                ("fake_device_us", c_int32), ("hbm_budget_bytes", c_int64), ("deadline_us", c_int32),
+                ("slot_timeout_us", c_int32)]
 
 
 class bf_job(ctypes.Structure):
@@ -492,7 +513,12 @@ class bf_replay_item(ctypes.Structure):
 class bf_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("launches", c_int64),
                 ("rejected_budget", c_int64), ("rejected_full", c_int64), ("budget_waits", c_int64),
-                ("max_inflight_bytes", c_int64), ("max_busy_slots", c_int32), ("max_jobs_per_launch", c_int32)]
+                ("max_inflight_bytes", c_int64), ("max_busy_slots", c_int32), ("max_jobs_per_launch", c_int32),
+                ("over_deadline", c_int64), ("timed_out", c_int64), ("deadline_ns", c_int64),
+                ("slot_timeout_ns", c_int64), ("worst_latency_ns", c_int64), ("worst_submit_ns", c_int64),
+                ("worst_queue_ns", c_int64), ("worst_launch_ns", c_int64), ("worst_device_ns", c_int64),
+                ("over_by_submit", c_int64), ("over_by_queue", c_int64), ("over_by_launch", c_int64),
+                ("over_by_device", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -527,9 +553,11 @@ def bf_now_ns() -> int:
 
 
 def bf_serve_create(plan, n_slots: int = 4, max_batch_jobs: int = 16, queue_capacity: int = 4096,
-                    hbm_budget_bytes: int = 8 << 30, fake_device_us: int = 0) -> int:
+                    hbm_budget_bytes: int = 8 << 30, fake_device_us: int = 0, deadline_us: int = 0,
+                    slot_timeout_us: int = 0) -> int:
     L = _serve_sigs(lib())
-    cfg = bf_serve_config(n_slots, max_batch_jobs, queue_capacity, fake_device_us, hbm_budget_bytes)
+    cfg = bf_serve_config(n_slots, max_batch_jobs, queue_capacity, fake_device_us, hbm_budget_bytes,
+                          deadline_us, slot_timeout_us)
     h = c_void_p()
     _check(L.bf_serve_create(plan, ctypes.byref(cfg), ctypes.byref(h)), plan)
     return h.value
@@ -561,7 +589,9 @@ def bf_submit(srv, groups, prec: int, S_dev, R_dev, cell: int = 0, arrival_ns: i
 
 
 def bf_poll(srv, ticket: int) -> Tuple[bool, Optional[float]]:
-    """(done, latency_us); the ticket is retired once done is returned True."""
+    """(done, latency_us); the ticket is retired once done is returned True.
+    A job that finished with an error (BF_ETIMEOUT from the watchdog, BF_ECUDA)
+    raises BfError with that status; its ticket is retired too."""
     d, lat = c_int(), c_double()
     st = _serve_sigs(lib()).bf_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(lat))
     if st != BF_OK:

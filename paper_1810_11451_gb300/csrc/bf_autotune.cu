@@ -159,8 +159,13 @@ extern "C" bf_status bf_tune_save(bf_plan plan, const char *path) {
     FILE *fh = fopen(path, "w");
     if (!fh) return bf_fail(plan, BF_EINVAL, "cannot open %s for writing", path);
     const TuneTable &T = plan->tune;
-    fprintf(fh, "{\n  \"format\": \"libbf-tune-1\",\n  \"sm_count\": %d,\n  \"simt_ctas_per_sm\": %d,\n",
-            plan->sm_count, T.simt_ctas_per_sm);
+    std::string name = plan->device_name;
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+    fprintf(fh, "{\n  \"format\": \"libbf-tune-2\",\n");
+    fprintf(fh, "  \"target\": {\"device\": \"%s\", \"cc\": %d, \"sm_count\": %d},\n", name.c_str(), plan->cc,
+            plan->sm_count);
+    fprintf(fh, "  \"simt_ctas_per_sm\": %d,\n", T.simt_ctas_per_sm);
     fprintf(fh, "  \"f_bucket_upper\": [0, 8, 16, 24, 36],\n  \"precisions\": [\n");
     for (int p = 0; p < N_PREC; ++p) {
         fprintf(fh, "    {\"precision\": %d, \"tuned\": %d, \"ns_per_block\": [", p, T.tuned[p] ? 1 : 0);
@@ -174,20 +179,68 @@ extern "C" bf_status bf_tune_save(bf_plan plan, const char *path) {
     return ok ? BF_OK : bf_fail(plan, BF_EINVAL, "write to %s failed", path);
 }
 
-// Reads the format bf_tune_save writes (keys in that order).
-extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
-    if (!plan || !path) return bf_fail(plan, BF_EINVAL, "NULL argument");
+namespace {
+
+bool read_file(const char *path, std::string &txt) {
     FILE *fh = fopen(path, "r");
-    if (!fh) return bf_fail(plan, BF_EINVAL, "cannot open %s", path);
-    std::string txt;
+    if (!fh) return false;
     char buf[4096];
     size_t n;
     while ((n = fread(buf, 1, sizeof buf, fh)) > 0) txt.append(buf, n);
     fclose(fh);
+    return true;
+}
+
+// The target a table was measured on: the "target" object bf_tune_save writes.
+bool parse_target(const std::string &txt, std::string &name, int &cc, int &sms) {
+    static const char key[] = "\"target\": {\"device\": \"";
+    size_t pos = txt.find(key);
+    if (pos == std::string::npos) return false;
+    pos += sizeof key - 1;
+    const size_t end = txt.find('"', pos);
+    if (end == std::string::npos) return false;
+    name = txt.substr(pos, end - pos);
+    return sscanf(txt.c_str() + end, "\", \"cc\": %d, \"sm_count\": %d}", &cc, &sms) == 2;
+}
+
+// BF_OK when the table at `txt` was measured on this target, else BF_EINVAL
+// with the reason (errors are reported on `plan`, which may be NULL).
+bf_status check_target(bf_plan plan, const char *path, const std::string &txt, const char *device, int cc,
+                       int sm_count) {
+    if (txt.find("\"libbf-tune-2\"") == std::string::npos)
+        return bf_fail(plan, BF_EINVAL, "%s: not a libbf tune table with a recorded target (libbf-tune-2)", path);
+    std::string name;
+    int tcc = 0, tsms = 0;
+    if (!parse_target(txt, name, tcc, tsms)) return bf_fail(plan, BF_EINVAL, "%s: unreadable target", path);
+    if (name != device || tcc != cc || tsms != sm_count)
+        return bf_fail(plan, BF_EINVAL,
+                       "%s: measured on \"%s\" (sm_%d, %d SMs), not on this target \"%s\" (sm_%d, %d SMs)", path,
+                       name.c_str(), tcc, tsms, device, cc, sm_count);
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_tune_check_target(const char *path, const char *device_name, int32_t cc,
+                                          int32_t sm_count) {
+    if (!path || !device_name) return bf_fail(nullptr, BF_EINVAL, "NULL argument");
+    std::string txt;
+    if (!read_file(path, txt)) return bf_fail(nullptr, BF_EINVAL, "cannot open %s", path);
+    return check_target(nullptr, path, txt, device_name, cc, sm_count);
+}
+
+// Reads the format bf_tune_save writes (keys in that order), after checking
+// that it was measured on this plan's device.
+extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
+    if (!plan || !path) return bf_fail(plan, BF_EINVAL, "NULL argument");
+    std::string txt;
+    if (!read_file(path, txt)) return bf_fail(plan, BF_EINVAL, "cannot open %s", path);
     auto bad = [&](const char *why) { return bf_fail(plan, BF_EINVAL, "%s: %s", path, why); };
-    if (txt.find("\"libbf-tune-1\"") == std::string::npos) return bad("not a libbf tune table");
+    bf_status ts = check_target(plan, path, txt, plan->device_name.c_str(), plan->cc, plan->sm_count);
+    if (ts != BF_OK) return ts;
+    size_t pos;
     TuneTable T;
-    size_t pos = txt.find("\"simt_ctas_per_sm\":");
+    pos = txt.find("\"simt_ctas_per_sm\":");
     if (pos == std::string::npos || sscanf(txt.c_str() + pos + 19, "%d", &T.simt_ctas_per_sm) != 1 ||
         T.simt_ctas_per_sm < 1 || T.simt_ctas_per_sm > 16)
         return bad("simt_ctas_per_sm");
@@ -195,10 +248,7 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
         char key[32];
         snprintf(key, sizeof key, "\"precision\": %d,", p);
         pos = txt.find(key);
-        if (pos == std::string::npos) {
-            if (p >= BF_FP32_3M) continue;  // tables written before these forms existed
-            return bad("missing precision");
-        }
+        if (pos == std::string::npos) return bad("missing precision");
         int tuned = 0;
         size_t q = txt.find("\"tuned\":", pos);
         if (q == std::string::npos || sscanf(txt.c_str() + q + 8, "%d", &tuned) != 1) return bad("tuned");

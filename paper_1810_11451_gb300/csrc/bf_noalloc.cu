@@ -23,14 +23,9 @@ constexpr int MAX_DEVICES = 64;
 // Scratch shared by every call: 2 doubles per block, then the 2 totals.
 static __device__ __align__(256) double g_errnorm_scratch[2 * BF_ERRNORM_NOALLOC_MAX_BLOCKS + 2];
 
-// Per-device set-up: the scratch array's device address (in host code the
-// symbol is only a host-side stand-in) and the SM count for the grid.
-struct DevState {
-    bool ready = false;
-    double *scratch = nullptr;
-    int sms = 0;
-};
-DevState g_dev[MAX_DEVICES];
+// Per-device SM count for the grid (an attribute of the device ordinal, which
+// no reset or context change alters).
+int g_sms[MAX_DEVICES];
 std::mutex g_mu;
 
 }  // namespace
@@ -48,33 +43,33 @@ extern "C" bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev,
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES) return bf_fail(nullptr, BF_ECUDA, "device ordinal %d out of range", dev);
-    DevState st;
+    // The array's device address, looked up on every call for the current
+    // device and context (in host code the symbol is only a host-side stand-in):
+    // a cached address would outlive a cudaDeviceReset or belong to another
+    // context. The first lookup on a device may load the library's device code,
+    // so make the first call before any stream capture.
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_errnorm_scratch);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    int sms = 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_dev[dev].ready) {
-            // First call on this device, which is current: look the array's
-            // device address up once. Make this first call before any capture.
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_errnorm_scratch);
-            if (e != cudaSuccess)
-                return bf_fail(nullptr, BF_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            int sms = 0;
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess)
+        if (g_sms[dev] == 0) {
+            e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) {
+                g_sms[dev] = 0;
                 return bf_fail(nullptr, BF_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-            g_dev[dev].scratch = static_cast<double *>(p);
-            g_dev[dev].sms = sms;
-            g_dev[dev].ready = true;
+            }
         }
-        st = g_dev[dev];
+        sms = g_sms[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
     // Nothing needs clearing: the kernels write every per-block pair they later
     // read, and the totals, before anything reads them.
-    double *per_block = st.scratch;
-    double *total = st.scratch + 2 * BF_ERRNORM_NOALLOC_MAX_BLOCKS;
+    double *per_block = static_cast<double *>(p);
+    double *total = per_block + 2 * BF_ERRNORM_NOALLOC_MAX_BLOCKS;
     e = bfi::launch_errnorm((const float2 *)R_dev, (const double2 *)Rref_dev, n_blocks, per_block, total,
-                            st.sms * 8, s);
+                            sms * 8, s);
     if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "error-norm launch: %s", cudaGetErrorString(e));
     e = cudaMemcpyAsync(total_host, total, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -147,6 +147,8 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
     bf_plan p = new bf_plan_s();
     p->device = dev;
     p->sm_count = prop.multiProcessorCount;
+    p->cc = prop.major * 10 + prop.minor;
+    p->device_name = prop.name;
     p->n_ant = n_ant;
     p->f_max = f_max;
     p->b = b;

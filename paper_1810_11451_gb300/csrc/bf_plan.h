@@ -87,6 +87,8 @@ struct StageBuf {
 
 struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
+    int cc = 0;                 // compute capability, major * 10 + minor
+    std::string device_name;    // cudaDeviceProp::name (the tune table's target)
     int simt_resident = 2;  // CTAs of the CUDA-core kernels that fit on one SM (the smaller of the two)
     std::string err;
     std::mutex err_mu;  // err is written from the caller's and a serving engine's threads

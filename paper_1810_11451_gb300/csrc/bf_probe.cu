@@ -1,0 +1,79 @@
+// bf_probe.cu -- bf_measure_fp32_peak: the FP32 fused multiply-add rate of the
+// CUDA cores, measured on the current device. It is the roofline denominator
+// of the plain FP32 product form (BF_FP32), whose 22.4 flop per byte at f = 36
+// puts it above the CUDA-core ridge point: its bound is FMA issue, not HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bf.h"
+#include "bf_plan.h"
+
+namespace {
+
+constexpr int CHAINS = 8;    // independent FMA chains per thread (covers the FMA latency)
+constexpr int THREADS = 256;
+constexpr int CTAS_PER_SM = 4;
+
+// Every thread runs CHAINS independent chains a <- a * b + c for `iters`
+// rounds: 2 * CHAINS * iters flop per thread, no memory traffic inside the
+// loop. b is just below 1 and c small, so the values stay finite and normal.
+// The final store is conditional on a value no chain reaches, so the compiler
+// cannot drop the loop, and it never writes in practice.
+__global__ void __launch_bounds__(THREADS) bf_ffma_peak_kernel(float *sink, int iters, float b, float c) {
+    float a[CHAINS];
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < CHAINS; ++k) a[k] = __fmaf_rn(a[k], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) s += a[k];
+    if (s == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *tflops_host, double *ms_host,
+                                          void *stream) {
+    if (!tflops_host || iters < 1 || iters > (1 << 24) || reps < 1 || reps > 1000)
+        return bf_fail(nullptr, BF_EINVAL, "bf_measure_fp32_peak: iters in [1, 2^24], reps in [1, 1000], "
+                                           "tflops_host not NULL");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "device query: %s", cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = sms * CTAS_PER_SM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return bf_fail(nullptr, BF_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
+    float best_ms = 0.f;
+    // one warm-up launch, then the best of `reps` timed launches
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e != cudaSuccess) break;
+        bf_ffma_peak_kernel<<<grid, THREADS, 0, s>>>(nullptr, iters, 0.9999999f, 1e-7f);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0) best_ms = (best_ms == 0.f) ? ms : std::min(best_ms, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "FMA probe: %s", cudaGetErrorString(e));
+    const double flop = 2.0 * CHAINS * 4 * (double)iters * (double)grid * THREADS;
+    *tflops_host = flop / (best_ms * 1e-3) / 1e12;
+    if (ms_host) *ms_host = best_ms;
+    return BF_OK;
+}

@@ -1,6 +1,7 @@
 // bf_serve.cu -- the continuous-batching serving loop of include/bf_serve.h:
 // FIFO queue, HBM-budget admission, launch slots (one stream each), merged
-// launches of the persistent product kernel, completion by event polling.
+// launches of the persistent product kernel, completion by event polling, a
+// watchdog on launches that do not complete and per-job deadline accounting.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +30,7 @@ struct JobRec {
     int32_t slot_lo = 0, slot_hi = 0;  // precoder slots read: [slot_lo, slot_hi)
     int64_t bytes = 0;
     int64_t arrival_ns = 0;
+    int64_t submit_ns = 0, admit_ns = 0, launched_ns = 0;
     int64_t done_ns = 0;
     int state = QUEUED;
     bool waited_budget = false;
@@ -40,6 +42,9 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     bool busy = false;
     int64_t fake_done_ns = 0;
+    int64_t launched_ns = 0;   // when the launch was enqueued (the watchdog's start)
+    bool timed_out = false;    // the watchdog failed its jobs; the launch still runs
+    int64_t held_bytes = 0;    // budget of those jobs, released when it completes
     std::vector<uint64_t> jobs;
 };
 
@@ -76,6 +81,30 @@ struct bf_server_s {
     std::vector<bf_group> merged;
     std::vector<std::pair<int32_t, int32_t>> merged_slots;  // slot ranges of the merged jobs
 };
+
+// A job leaves the engine (completed, failed or timed out): its latency is
+// accounted against the deadline and the worst job's breakdown kept.
+static void account_done(bf_server_s *srv, JobRec &j) {
+    const int64_t lat = j.done_ns - j.arrival_ns;
+    const int64_t part[4] = {j.submit_ns - j.arrival_ns,
+                             j.admit_ns ? j.admit_ns - j.submit_ns : j.done_ns - j.submit_ns,
+                             j.launched_ns && j.admit_ns ? j.launched_ns - j.admit_ns : 0,
+                             j.launched_ns ? j.done_ns - j.launched_ns : 0};
+    bf_serve_stats &st = srv->stats;
+    if (lat > st.deadline_ns) {
+        st.over_deadline++;
+        const int k = (int)(std::max_element(part, part + 4) - part);
+        int64_t *by[4] = {&st.over_by_submit, &st.over_by_queue, &st.over_by_launch, &st.over_by_device};
+        ++*by[k];
+    }
+    if (lat > st.worst_latency_ns) {
+        st.worst_latency_ns = lat;
+        st.worst_submit_ns = part[0];
+        st.worst_queue_ns = part[1];
+        st.worst_launch_ns = part[2];
+        st.worst_device_ns = part[3];
+    }
+}
 
 extern "C" int64_t bf_now_ns(void) {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -162,7 +191,30 @@ static void dispatcher(bf_server srv) {
             const bf_status st = done_st[k];
             if (!done_flag[k]) {
                 any_busy = true;
+                // watchdog: give the launch's jobs up, keep the slot and their
+                // budget until the device is done with their buffers
+                if (!sl.timed_out && now - sl.launched_ns > srv->stats.slot_timeout_ns) {
+                    for (uint64_t t : sl.jobs) {
+                        JobRec &j = srv->jobs[t];
+                        j.state = DONE;
+                        j.status = BF_ETIMEOUT;
+                        j.done_ns = now;
+                        sl.held_bytes += j.bytes;
+                        srv->stats.completed++;
+                        srv->stats.timed_out++;
+                        account_done(srv, j);
+                    }
+                    sl.jobs.clear();
+                    sl.timed_out = true;
+                    progressed = true;
+                    srv->cv_done.notify_all();
+                }
                 continue;
+            }
+            if (sl.timed_out) {  // a given-up launch finally completed
+                srv->inflight_bytes -= sl.held_bytes;
+                sl.held_bytes = 0;
+                sl.timed_out = false;
             }
             for (uint64_t t : sl.jobs) {
                 JobRec &j = srv->jobs[t];
@@ -171,6 +223,7 @@ static void dispatcher(bf_server srv) {
                 j.done_ns = now;
                 srv->inflight_bytes -= j.bytes;
                 srv->stats.completed++;
+                account_done(srv, j);
             }
             sl.jobs.clear();
             sl.busy = false;
@@ -206,9 +259,11 @@ static void dispatcher(bf_server srv) {
             }
             srv->merged.clear();
             srv->merged_slots.clear();
+            const int64_t t_admit = bf_now_ns();
             for (uint64_t t : take) {
                 JobRec &j = srv->jobs[t];
                 j.state = RUNNING;
+                j.admit_ns = t_admit;
                 srv->merged.insert(srv->merged.end(), j.groups.begin(), j.groups.end());
                 srv->merged_slots.emplace_back(j.slot_lo, j.slot_hi);
             }
@@ -222,7 +277,10 @@ static void dispatcher(bf_server srv) {
             ranges.swap(srv->merged_slots);
             lk.unlock();
             const bf_status st = launch_slot(srv, *free_slot, prec, groups, ranges);
+            const int64_t t_launched = bf_now_ns();
             lk.lock();
+            free_slot->launched_ns = t_launched;
+            for (uint64_t t : take) srv->jobs[t].launched_ns = t_launched;
             srv->stats.launches++;
             srv->stats.max_jobs_per_launch = std::max(srv->stats.max_jobs_per_launch, (int32_t)take.size());
             int busy = 0;
@@ -236,6 +294,7 @@ static void dispatcher(bf_server srv) {
                     j.done_ns = bf_now_ns();
                     srv->inflight_bytes -= j.bytes;
                     srv->stats.completed++;
+                    account_done(srv, j);
                 }
                 free_slot->jobs.clear();
                 free_slot->busy = false;
@@ -262,13 +321,15 @@ extern "C" bf_status bf_serve_create(bf_plan plan, const bf_serve_config *cfg, b
     if (!out || !cfg) return bf_fail(plan, BF_EINVAL, "NULL argument");
     *out = nullptr;
     if (cfg->n_slots < 1 || cfg->n_slots > 8 || cfg->max_batch_jobs < 1 || cfg->queue_capacity < 1 ||
-        cfg->hbm_budget_bytes <= 0 || cfg->fake_device_us < 0)
+        cfg->hbm_budget_bytes <= 0 || cfg->fake_device_us < 0 || cfg->deadline_us < 0 || cfg->slot_timeout_us < 0)
         return bf_fail(plan, BF_EINVAL, "bad serving configuration");
     if (!plan && cfg->fake_device_us == 0) return bf_fail(nullptr, BF_EINVAL, "plan is NULL");
     bf_server s = new bf_server_s();
     s->plan = plan;
     s->cfg = *cfg;
     s->fake = cfg->fake_device_us > 0;
+    s->stats.deadline_ns = (int64_t)(cfg->deadline_us ? cfg->deadline_us : 500) * 1000;
+    s->stats.slot_timeout_ns = (int64_t)(cfg->slot_timeout_us ? cfg->slot_timeout_us : 50000) * 1000;
     s->slots.resize(cfg->n_slots);
     if (!s->fake) {
         bf_status st = plan_ensure_device(plan);
@@ -360,6 +421,7 @@ extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticke
     if (job->n_groups && (!job->S_dev || !job->R_dev || ((uintptr_t)job->S_dev & 15) || ((uintptr_t)job->R_dev & 15)))
         return bf_fail(srv->plan, BF_EINVAL, "S_dev and R_dev must be non-NULL and 16-byte aligned");
     JobRec rec;
+    rec.submit_ns = bf_now_ns();
     {
         std::lock_guard<std::mutex> sl(srv->slot_mu);
         const int *f_slot = srv->fake ? nullptr : srv->plan->f_slot.data();
@@ -383,7 +445,7 @@ extern "C" bf_status bf_submit(bf_server srv, const bf_job *job, uint64_t *ticke
     }
     rec.cell = job->cell;
     rec.prec = job->prec;
-    rec.arrival_ns = job->arrival_ns ? job->arrival_ns : bf_now_ns();
+    rec.arrival_ns = job->arrival_ns ? job->arrival_ns : rec.submit_ns;
     std::lock_guard<std::mutex> lk(srv->mu);
     if (rec.bytes > srv->cfg.hbm_budget_bytes) {
         srv->stats.rejected_budget++;

@@ -172,6 +172,13 @@ class ServingSim:
             "launches": stats["launches"], "max_busy_slots": stats["max_busy_slots"],
             "max_jobs_per_launch": stats["max_jobs_per_launch"], "budget_waits": stats["budget_waits"],
             "max_inflight_bytes": stats["max_inflight_bytes"],
+            "engine": {"over_deadline": stats["over_deadline"], "timed_out": stats["timed_out"],
+                       "deadline_us": stats["deadline_ns"] * 1e-3, "completed": stats["completed"],
+                       "worst_us": {k: stats[f"worst_{k}_ns"] * 1e-3
+                                    for k in ("latency", "submit", "queue", "launch", "device")},
+                       "over_deadline_by_largest_part": {k: stats[f"over_by_{k}"]
+                                                         for k in ("submit", "queue", "launch", "device")},
+                       "note": "counted by the server over every job, warm-up TTIs included"},
             **({"samples": samples} if sample_every else {}),
         }
 

@@ -170,3 +170,32 @@ def test_filter_create_rejects_size_before_cuda(bf):
     assert "2048" in bf.bf_filter_last_error(None)
     assert L.bf_filter_create(2048, None) == bf.BF_EINVAL
     assert L.bf_filter_destroy(None) == bf.BF_OK
+
+
+def _table(path, device="NVIDIA GB300", cc=103, sms=152, fmt="libbf-tune-2"):
+    prec = ",\n".join(f'    {{"precision": {p}, "tuned": 1, "ns_per_block": [1.0, 2.0, 3.0, 4.0, 5.0], '
+                      f'"tile_blocks": [2, 2, 2, 2, 2]}}' for p in range(6))
+    with open(path, "w") as fh:
+        fh.write(f'{{\n  "format": "{fmt}",\n  "target": {{"device": "{device}", "cc": {cc}, "sm_count": {sms}}},\n'
+                 f'  "simt_ctas_per_sm": 2,\n  "f_bucket_upper": [0, 8, 16, 24, 36],\n  "precisions": [\n'
+                 f'{prec}\n  ]\n}}\n')
+
+
+def test_tune_table_is_keyed_by_target(bf, tmp_path):
+    """A tune table names the target it was measured on (device name, compute
+    capability, SM count); a table from another GPU, or one without a target,
+    is refused before anything is loaded."""
+    p = str(tmp_path / "t.json")
+    _table(p)
+    bf.bf_tune_check_target(p, "NVIDIA GB300", 103, 152)
+    for other in [("NVIDIA GB300", 103, 148), ("NVIDIA B200", 100, 148), ("NVIDIA GB300", 100, 152),
+                  ("NVIDIA GB200", 103, 152)]:
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_tune_check_target(p, *other)
+        assert ei.value.status == bf.BF_EINVAL and "not on this target" in str(ei.value)
+    _table(p, fmt="libbf-tune-1")
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_tune_check_target(p, "NVIDIA GB300", 103, 152)
+    assert ei.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BfError):
+        bf.bf_tune_check_target(str(tmp_path / "missing.json"), "NVIDIA GB300", 103, 152)

@@ -60,6 +60,80 @@ def _assert_close(R, ref, tol, what):
     return e
 
 
+# the oracle's encoding of each tensor-core form
+ENC = {bf.BF_BF16: "bf16", bf.BF_FP16: "fp16", bf.BF_BF16X3: "bf16x3", bf.BF_TF32X3: "tf32x3"}
+# what separates a tensor-core result from the FP64 product of the oracle's
+# encodings of the same operands: FP32 accumulation rounding only
+MECH_BOUND = 2e-6
+
+
+def _assert_per_block(R, ref, tol, what):
+    """Every block within tol of the oracle (relative Frobenius error of the
+    block); blocks whose reference is zero (f = 0) must be exactly zero."""
+    worst = 0.0
+    for g, (a, r) in enumerate(zip(R, ref)):
+        if a.size == 0:
+            continue
+        assert np.all(np.isfinite(a)), f"{what}: group {g}: unwritten (NaN) outputs"
+        num, den = oracle.errnorm_blocks(a, r)
+        zero = den == 0
+        assert np.all(num[zero] == 0), f"{what}: group {g}: nonzero R where the reference is zero"
+        if np.any(~zero):
+            e = np.sqrt(num[~zero] / den[~zero])
+            k = int(np.argmax(e))
+            assert e[k] <= tol, f"{what}: group {g} block {k}: error {e[k]:.3e} > {tol:.1e}"
+            worst = max(worst, float(e[k]))
+    return worst
+
+
+def _assert_mechanics(R, batch, prec, held, what, bound=MECH_BOUND):
+    """Every block against the FP64 product of the oracle's encodings of its
+    operands (held S: with its per-block scale; S encoded on chip: unscaled;
+    the precoder with its own power-of-two scale). Returns the worst block."""
+    name = ENC[prec]
+    pairs = [(0, 0), (0, 1), (1, 0)] if name in ("bf16x3", "tf32x3") else [(0, 0)]
+    wenc, worst = {}, 0.0
+    for g, (p, S) in enumerate(zip(batch.prec, batch.S)):
+        if S.shape[0] == 0 or S.shape[1] == 0:
+            continue
+        if p not in wenc:
+            sw, wpl = oracle.quantize_planes(batch.W[p].astype(np.complex64), name)
+            wenc[p] = (sw, [a + 1j * b for a, b in wpl])
+        sw, Wt = wenc[p]
+        ss, spl = oracle.quantize_blocks(S, name, scaled=held)
+        exp = oracle.apply_terms(Wt, [a + 1j * b for a, b in spl], pairs, sw) * ss[:, None, None]
+        num, den = oracle.errnorm_blocks(R[g], exp)
+        e = np.sqrt(num / den)
+        k = int(np.argmax(e))
+        assert e[k] < bound, f"{what}: group {g} block {k}: mechanics error {e[k]:.2e} >= {bound:.0e}"
+        worst = max(worst, float(e[k]))
+    return worst
+
+
+def _check_full(R, batch, prec, held, what, ref_c64, ref_unrounded):
+    """The full-size checks of one result: the batch error, every block's
+    error against the oracle at the form's tolerance and, for the tensor-core
+    forms, every block against the FP64 product of its encoded operands."""
+    ref = ref_c64 if prec in ACCURATE else ref_unrounded
+    e = _assert_close(R, ref, _tol(prec), what)
+    wb = _assert_per_block(R, ref, _tol(prec), what)
+    wm = _assert_mechanics(R, batch, prec, held, what) if prec in ENC else None
+    print(f"{what}: batch {e:.3e}, worst block {wb:.3e}" + ("" if wm is None else f", worst mechanics {wm:.2e}"))
+
+
+_REFS = {}
+
+
+def _full_refs(key, make):
+    """A full-size workload and its two oracle results (complex64-rounded
+    inputs, and the unrounded inputs), computed once per module."""
+    if key not in _REFS:
+        _REFS.clear()  # one full-size workload held at a time
+        batch = make()
+        _REFS[key] = (batch, _ref(batch), oracle.apply_batch(batch))
+    return _REFS[key]
+
+
 @pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
 def test_exact_integers_bitwise(plan, name, prec, held):
     batch = wl.config_exact_integer()
@@ -234,15 +308,14 @@ def test_host_path_scattered_buffers(plan):
     assert np.all(np.isnan(R_h.numpy()[~written.reshape(-1, 4).all(axis=1)]))
 
 
-def test_fullband_full_size(plan):
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
+def test_fullband_full_size(plan, name, prec, held):
     """The full-band f = 36 workload at full size (273 x 14 = 3,822 blocks) in
-    the launch configuration the bench times, checked in full against the oracle."""
-    batch = wl.config_fullband()
-    ref = _ref(batch)
-    for prec in ACCURATE:
-        R = run(plan, batch, prec, torch, mode="batch")
-        e = _assert_close(R, ref, _tol(prec), f"fullband prec {prec}")
-        print(f"full band prec {prec}: rel err {e:.3e}")
+    the launch configuration the bench times, checked in full against the
+    oracle, block by block."""
+    batch, ref, ref64 = _full_refs("fullband", wl.config_fullband)
+    R = run(plan, batch, prec, torch, held=held, mode="batch")
+    _check_full(R, batch, prec, held, f"fullband {name}", ref, ref64)
 
 
 def test_errnorm_matches_numpy(plan):
@@ -321,6 +394,16 @@ def test_autotune_keeps_results_and_round_trips(plan, tmp_path):
         got = [bf.bf_tune_query(other, bf.BF_BF16X3, f) for f in (0, 8, 16, 24, 36)]
         assert all(abs(a["ns_per_block"] - b["ns_per_block"]) < 1e-5 and a["tile_blocks"] == b["tile_blocks"]
                    for a, b in zip(saved, got))
+        # the same table measured on another target is refused, and the plan keeps its table
+        txt = open(path).read()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert f'"sm_count": {sms}' in txt
+        with open(path, "w") as fh:
+            fh.write(txt.replace(f'"sm_count": {sms}', f'"sm_count": {sms - 4}'))
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_tune_load(other, path)
+        assert ei.value.status == bf.BF_EINVAL and "not on this target" in str(ei.value)
+        assert bf.bf_tune_query(other, bf.BF_BF16X3, 36)["ns_per_block"] == got[-1]["ns_per_block"]
         with open(path, "w") as fh:
             fh.write("{}")
         with pytest.raises(bf.BfError):
@@ -329,42 +412,38 @@ def test_autotune_keeps_results_and_round_trips(plan, tmp_path):
         bf.bf_plan_destroy(other)
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[0], FORMS[1], FORMS[4], FORMS[7], FORMS[8]],
-                         ids=["fp32", "bf16x3", "bf16_held", "fp32_3m", "tf32x3"])
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
 def test_uneven_full_size(plan, name, prec, held):
     """The uneven workload at full size (16,384 blocks) in one persistent launch,
-    checked in full against the oracle."""
-    batch = wl.config_uneven()
+    checked in full against the oracle, block by block (f = 0 blocks exactly 0)."""
+    batch, ref, ref64 = _full_refs("uneven", wl.config_uneven)
     R = run(plan, batch, prec, torch, held=held, mode="batch")
-    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
-    e = _assert_close(R, ref, _tol(prec), name)
-    print(f"uneven full size {name}: {e:.3e}")
+    _check_full(R, batch, prec, held, f"uneven full size {name}", ref, ref64)
 
 
-@pytest.mark.parametrize("name,prec", [("bf16x3", bf.BF_BF16X3), ("bf16", bf.BF_BF16), ("tf32x3", bf.BF_TF32X3)])
+@pytest.mark.parametrize("name,prec", [("bf16x3", bf.BF_BF16X3), ("bf16", bf.BF_BF16), ("fp16", bf.BF_FP16),
+                                       ("tf32x3", bf.BF_TF32X3)])
 def test_uneven_full_size_repeatable(plan, name, prec):
     """Pipeline races show up as a few wrong blocks that change from run to run:
     the full-size uneven batch (1- and 2-block tiles, f from 0 to 36, many
-    precoder switches per CTA) must give the same bits five times over."""
-    batch = wl.config_uneven()
+    precoder switches per CTA) must give the same bits five times over, and the
+    first run is checked block by block."""
+    batch, ref, ref64 = _full_refs("uneven", wl.config_uneven)
     first = run(plan, batch, prec, torch, mode="batch")
-    ref = _ref(batch) if prec in ACCURATE else oracle.apply_batch(batch)
-    _assert_close(first, ref, _tol(prec), name)
+    _assert_per_block(first, ref if prec in ACCURATE else ref64, _tol(prec), name)
     for rep in range(4):
         again = run(plan, batch, prec, torch, mode="batch" if rep % 2 else "apply", set_w=False)
         for g, (x, y) in enumerate(zip(first, again)):
             assert np.array_equal(x.view(np.uint64), y.view(np.uint64)), f"{name}: group {g} differs on repeat {rep}"
 
 
-@pytest.mark.parametrize("name,prec,held", [FORMS[1], FORMS[2], FORMS[4], FORMS[6]],
-                         ids=["bf16x3", "bf16x3_held", "bf16_held", "fp16_held"])
+@pytest.mark.parametrize("name,prec,held", FORMS, ids=[f[0] for f in FORMS])
 def test_reduced_full_size(plan, name, prec, held):
-    """The reduced-precision workload at full size (30,576 blocks, 2,184 precoders)."""
-    batch = wl.config_reduced()
+    """The reduced-precision workload at full size (30,576 blocks, 2,184
+    precoders), block by block."""
+    batch, ref, ref64 = _full_refs("reduced", wl.config_reduced)
     R = run(plan, batch, prec, torch, held=held, mode="batch")
-    ref = _ref(batch) if prec == bf.BF_BF16X3 else oracle.apply_batch(batch)
-    e = _assert_close(R, ref, _tol(prec), name)
-    print(f"reduced full size {name}: {e:.3e}")
+    _check_full(R, batch, prec, held, f"reduced full size {name}", ref, ref64)
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable(plan):

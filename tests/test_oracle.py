@@ -484,3 +484,79 @@ def test_split_product_within_bound(oracle_lib):
     R1 = oracle.apply_terms(Wt, St, [(0, 0)], sw * ss, oracle_lib)
     e1 = oracle.rel_frobenius([R1], [ref])
     assert 2.0 ** -12 < e1 < 2.0 ** -7  # single pass: bf16 rounding of both operands
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "bf16x3", "tf32x3"])
+def test_quantize_planes_scale_hand_worked(prec):
+    """The per-block scale is 2^ceil(log2 m) with m the largest of |Re| and |Im|
+    over the block (component-wise, not the complex modulus), and the planes are
+    the block divided by it. Each case below is worked by hand; every encoded
+    value is exactly representable, so the planes are checked exactly too.
+      * the largest component is imaginary: [0.25 + 2.5j, -0.5 + 0.125j]:
+        m = 2.5 -> 4 (Re alone would give 0.5);
+      * |z| crosses a power of two that no component reaches: [0.75 + 0.75j]:
+        m = 0.75 -> 1 (the modulus 1.06 would give 2);
+      * exact powers of two: m = 1 -> 1, m = 4 (a negative real part) -> 4,
+        m = 2^-3 -> 2^-3; one step above a power of two: m = 2 + 2^-21 -> 4;
+      * an all-zero block keeps the scale 1."""
+    cases = [
+        (np.array([0.25 + 2.5j, -0.5 + 0.125j]), 4.0, [0.0625, -0.125], [0.625, 0.03125]),
+        (np.array([0.75 + 0.75j]), 1.0, [0.75], [0.75]),
+        (np.array([1.0 + 0.5j, 0.25 - 1.0j]), 1.0, [1.0, 0.25], [0.5, -1.0]),
+        (np.array([-4.0 + 1.0j, 2.0 - 0.5j]), 4.0, [-1.0, 0.5], [0.25, -0.125]),
+        (np.array([0.125 - 0.0625j]), 0.125, [1.0], [-0.5]),
+        (np.array([0.5 + (2.0 + 2.0 ** -21) * 1j]), 4.0, [0.125], [None]),
+        (np.zeros(3, complex), 1.0, [0.0] * 3, [0.0] * 3),
+    ]
+    for x, s_want, re_want, im_want in cases:
+        blk = x.astype(np.complex64).reshape(1, -1)
+        s, planes = oracle.quantize_planes(blk, prec)
+        assert s == s_want, (x, s, s_want)
+        re, im = planes[0]
+        for got, want in ((re.ravel(), re_want), (im.ravel(), im_want)):
+            for g, w in zip(got, want):
+                if w is not None:
+                    assert g == np.float32(w), (x, prec, g, w)
+        if len(planes) > 1:  # split forms: exactly representable values leave no lo term
+            lo_re, lo_im = planes[1]
+            exact = [w is not None for w in im_want]
+            assert np.all(lo_re == 0) and np.all(lo_im.ravel()[exact] == 0)
+        s1, _ = oracle.quantize_planes(blk, prec, scaled=False)
+        assert s1 == 1.0
+
+
+def test_quantize_planes_scale_is_per_block_component_maximum():
+    """Brute force over random blocks: the scale equals the smallest power of two
+    that is >= every |Re| and |Im| of the block (found by doubling from 2^-40),
+    and a block multiplied by 2^k gets 2^k times the scale and the same planes."""
+    rng = np.random.default_rng(41)
+    for _ in range(200):
+        amp = 2.0 ** rng.integers(-20, 20)
+        x = (amp * (rng.normal(size=(7, 9)) + 1j * rng.normal(size=(7, 9)) * rng.uniform(0, 3))).astype(np.complex64)
+        m = max(float(np.max(np.abs(x.real))), float(np.max(np.abs(x.imag))))
+        p = 2.0 ** -40
+        while p < m:
+            p *= 2.0
+        s, planes = oracle.quantize_planes(x, "bf16")
+        assert s == p
+        s2, planes2 = oracle.quantize_planes((x * np.float32(8.0)).astype(np.complex64), "bf16")
+        assert s2 == 8.0 * s
+        assert all(np.array_equal(a, b) for pa, pb in zip(planes, planes2) for a, b in zip(pa, pb))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "bf16x3", "tf32x3"])
+def test_quantize_blocks_is_quantize_planes_per_block(prec):
+    """The vectorised encoding equals the pinned per-block one, bit for bit,
+    on blocks of very different levels (one of them all zero), scaled and not."""
+    rng = np.random.default_rng(43)
+    S = (rng.normal(size=(12, 5, 7)) + 1j * rng.normal(size=(12, 5, 7))) * \
+        (2.0 ** rng.integers(-12, 12, size=12))[:, None, None]
+    S[4] = 0
+    S = S.astype(np.complex64)
+    for scaled in (True, False):
+        s, planes = oracle.quantize_blocks(S, prec, scaled)
+        for n in range(S.shape[0]):
+            s1, p1 = oracle.quantize_planes(S[n], prec, scaled)
+            assert s[n] == s1
+            for (re, im), (re1, im1) in zip(planes, p1):
+                assert np.array_equal(re[n], re1) and np.array_equal(im[n], im1)

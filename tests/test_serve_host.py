@@ -248,3 +248,80 @@ def test_replay_submits_each_job_at_its_arrival(bf):
         assert bf.bf_serve_replay(srv, (bf.bf_replay_item * 0)(), 0) == ([], 0)
     finally:
         bf.bf_serve_destroy(srv)
+
+
+def test_deadline_accounting_and_worst_job(bf):
+    """Jobs over the deadline are counted by the engine itself, and the worst
+    job's latency splits into submit, queue, launch and device time that add
+    up to it."""
+    srv = bf.bf_serve_create(None, n_slots=1, max_batch_jobs=1, hbm_budget_bytes=1 << 30, fake_device_us=3000,
+                             deadline_us=5000)
+    try:
+        ts = [bf.bf_submit(srv, job_groups(1), bf.BF_FP32, FAKE_S, FAKE_R) for _ in range(4)]
+        lats = [bf.bf_wait(srv, t, 5_000_000) for t in ts]
+        st = bf.bf_serve_get_stats(srv)
+        assert st["deadline_ns"] == 5_000_000 and st["slot_timeout_ns"] == 50_000_000
+        # one slot, 3 ms per launch: the first job is within 5 ms, the 3rd and 4th are not
+        assert st["over_deadline"] == sum(l > 5000 for l in lats) and st["over_deadline"] >= 2
+        assert lats[0] < 5000
+        assert abs(st["worst_latency_ns"] * 1e-3 - max(lats)) < 1.0
+        parts = st["worst_submit_ns"] + st["worst_queue_ns"] + st["worst_launch_ns"] + st["worst_device_ns"]
+        assert parts == st["worst_latency_ns"]
+        assert st["worst_queue_ns"] >= 2 * 2_900_000 and st["worst_device_ns"] >= 2_900_000
+        assert st["timed_out"] == 0
+        # the late jobs waited in the queue behind the single slot longer than their own launch ran
+        by = [st[k] for k in ("over_by_submit", "over_by_queue", "over_by_launch", "over_by_device")]
+        assert sum(by) == st["over_deadline"] and st["over_by_queue"] >= 1
+    finally:
+        bf.bf_serve_destroy(srv)
+    srv = bf.bf_serve_create(None, n_slots=2, hbm_budget_bytes=1 << 30, fake_device_us=100)
+    try:
+        t = bf.bf_submit(srv, job_groups(1), bf.BF_FP32, FAKE_S, FAKE_R)
+        bf.bf_wait(srv, t, 5_000_000)
+        st = bf.bf_serve_get_stats(srv)
+        assert st["deadline_ns"] == 500_000  # the 0.5 ms TTI by default
+    finally:
+        bf.bf_serve_destroy(srv)
+
+
+def test_watchdog_fails_a_launch_that_does_not_complete(bf):
+    """A launch not seen complete within slot_timeout_us fails its jobs with
+    BF_ETIMEOUT; its slot and budget stay held until the launch completes, and
+    the server then carries on. The fake device's 300 ms launch stands in for
+    a launch that hangs."""
+    per_job = 2 * R_BLOCK
+    srv = bf.bf_serve_create(None, n_slots=1, max_batch_jobs=4, hbm_budget_bytes=4 * per_job,
+                             fake_device_us=300_000, slot_timeout_us=20_000)
+    try:
+        bf.bf_serve_pause(srv, True)  # both jobs go into one launch
+        ts = [bf.bf_submit(srv, job_groups(2), bf.BF_FP32, FAKE_S, FAKE_R) for _ in range(2)]
+        t0 = time.monotonic()
+        bf.bf_serve_pause(srv, False)
+        for t in ts:
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_wait(srv, t, 2_000_000)
+            assert ei.value.status == bf.BF_ETIMEOUT
+        waited = time.monotonic() - t0
+        assert 0.015 <= waited < 0.25, waited  # given up at the watchdog's limit, not the launch's end
+        for t in ts:  # the tickets were retired with their status
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_poll(srv, t)
+            assert ei.value.status == bf.BF_ENOTFOUND
+        st = bf.bf_serve_get_stats(srv)
+        assert st["timed_out"] == 2 and st["completed"] == 2 and st["over_deadline"] == 2
+        # the budget of the given-up jobs is still held: a job that needs all of it waits
+        t_big = bf.bf_submit(srv, job_groups(8), bf.BF_FP32, FAKE_S, FAKE_R)
+        done, _ = bf.bf_poll(srv, t_big)
+        assert not done
+        # the stuck launch completes at 300 ms; the big job then runs (and is
+        # itself given up, its launch being as long)
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_wait(srv, t_big, 2_000_000)
+        assert ei.value.status == bf.BF_ETIMEOUT
+        assert time.monotonic() - t0 >= 0.29
+        assert bf.bf_serve_get_stats(srv)["timed_out"] == 3
+    finally:
+        bf.bf_serve_destroy(srv)  # waits for the last launch to complete
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_serve_create(None, fake_device_us=10, slot_timeout_us=-1)
+    assert ei.value.status == bf.BF_EINVAL

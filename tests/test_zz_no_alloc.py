@@ -6,8 +6,10 @@ callers have no plan or run where another allocator owns all device memory.
 bf_errnorm_noalloc serves them: no plan, no allocation, a fixed scratch array
 inside the library. This file checks, through the C ABI, that it returns what
 the plan-based bf_errnorm returns, on two calls in a row (the second call must
-not see the first call's scratch), and that it refuses batches larger than
-its scratch. The file is named so that pytest collects it last.
+not see the first call's scratch), that a call leaves the device's free
+memory unchanged (after a first call, which may load the library's device
+code), and that it refuses batches larger than its scratch. The file is named
+so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -43,6 +45,14 @@ def test_noalloc_matches_plan_errnorm_twice():
             got = bf.bf_errnorm_noalloc(Rd, Rrefd, n)
             assert np.allclose(got, want, rtol=RTOL, atol=0), (got, want)
         assert bf.bf_errnorm_noalloc(Rd, Rrefd, 0) == (0.0, 0.0)
+        # the promise itself: with the module loaded, a call takes no device memory
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        got = bf.bf_errnorm_noalloc(Rd, Rrefd, 41)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+        assert np.allclose(got, want, rtol=RTOL, atol=0)
         with pytest.raises(bf.BfError) as ei:
             bf.bf_errnorm_noalloc(Rd, Rrefd, bf.BF_ERRNORM_NOALLOC_MAX_BLOCKS + 1)
         assert ei.value.status == bf.BF_EINVAL
