@@ -507,7 +507,7 @@ def filter_cpu_leg(b):
                       "sample": f"{len(idx)} of {b.n_sig} blocks, direct FP64 circular convolution"}
 
 
-def filter_leg(torch, bf, b, sample, stream, steps=100):
+def filter_leg(torch, bf, b, sample, stream, steps=100, variant=None):
     """Fast-convolution filter y = IFFT(MULT(FFT(s))) (Sec. III, Fig. 4, N = 2048)
     over 16 slots x 64 antennas x 14 symbols = 14,336 blocks: 235 MB read and
     235 MB written per launch (inputs larger than L2), one fused kernel."""
@@ -516,6 +516,14 @@ def filter_leg(torch, bf, b, sample, stream, steps=100):
     h = to_device_c64(b.h, torch)
     bf.bf_filter_set_taps(f, h, len(b.h), stream)
     bf.bf_filter_set_s_independent(f)  # S is filled once, by a copy; the filter never writes it
+    # the building block for this size on this GPU (bit-identical candidates),
+    # unless a variant is named
+    if variant is None:
+        chosen = bf.bf_filter_autotune(f, b.n_sig, stream)
+        variants = {bf.FILTER_VARIANTS[v]: bf.bf_filter_tune_query(f, v)[0] for v in range(6)}
+    else:
+        bf.bf_filter_set_variant(f, variant)
+        chosen, variants = variant, None
     S = to_device_c64(b.s, torch)
     Y = torch.empty_like(S)
     for _ in range(5):
@@ -548,6 +556,7 @@ def filter_leg(torch, bf, b, sample, stream, steps=100):
     out = {"blocks": b.n_sig, "n": b.n, "kernel_ms": ms, "blocks_per_s": b.n_sig / ms * 1e3,
            "us_per_block_amortised": ms * 1e3 / b.n_sig, "gflops_conventional": b.flops() / ms / 1e6,
            "moved_bytes": moved, "moved_gbs": moved / ms / 1e6, "gpu_launches": int(launches), **small,
+           "variant": {"chosen": bf.FILTER_VARIANTS[chosen], "us_per_launch_tuned": variants},
            "paper_context_us_per_filter": {"original": 27, "intel_fft_library": 19,
                                            "hardware": "Intel Haswell (E9000 blade), one filter"}}
     if sample is not None:
@@ -629,6 +638,8 @@ def main():
     ap.add_argument("--sets", type=int, default=3, help="rotating buffer sets (3 keeps the working set above L2)")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven, reduced-precision and serving legs")
     ap.add_argument("--serving-ttis", type=int, default=20000, help="TTIs of the split-bf16 serving run")
+    ap.add_argument("--filter-variant", type=int, default=None,
+                    help="filter building block to time (default: the autotuner's choice)")
     ap.add_argument("--legs", default="fused_output,uneven,reduced,scaling,filter,serving",
                     help="comma-separated secondary workloads to run after the headline")
     args = ap.parse_args()
@@ -719,10 +730,13 @@ def main():
     fma = None
     if not args.no_plain:
         with ClockSampler(local) as fclk:
-            fma_tf, fma_ms = bf.bf_measure_fp32_peak(20000, 5, stream)
-        fma = {"tflops": fma_tf, "ms_per_launch": fma_ms, "clocks": fclk.summary(),
+            fma_tf, fma_ms = bf.bf_measure_fp32_peak(20000, 5, False, stream)
+            fma2_tf, _ = bf.bf_measure_fp32_peak(10000, 5, True, stream)
+        # the peak is the faster of scalar and packed FP32x2 FMAs
+        fma = {"tflops": max(fma_tf, fma2_tf), "scalar_tflops": fma_tf, "packed_tflops": fma2_tf,
+               "ms_per_launch": fma_ms, "clocks": fclk.summary(),
                "how": "bf_measure_fp32_peak: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
-                      "best of 5 launches (CUDA events)"}
+                      "scalar and packed FP32x2, best of 5 launches each (CUDA events)"}
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -778,7 +792,7 @@ def main():
         run_leg(legs, "scaling", scaling_leg, torch, bf, plan, b_scaling, ref_d, stream)
         del ref_d
     if b_filter is not None:
-        run_leg(legs, "filter", filter_leg, torch, bf, b_filter, filter_sample, stream)
+        run_leg(legs, "filter", filter_leg, torch, bf, b_filter, filter_sample, stream, 100, args.filter_variant)
     if extra and "serving" in want:
         run_leg(legs, "serving_bf16x3", serving_leg, torch, bf, args.serving_ttis, bf.BF_BF16X3)
         run_leg(legs, "serving_fp32", serving_leg, torch, bf, args.serving_ttis, bf.BF_FP32)

@@ -443,11 +443,13 @@ bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev, int64_t n_
  * 22.4 flop per algorithmic byte, above the CUDA-core ridge, so its bound is
  * FMA issue (Sec. III: the paper's improved kernel is built on FMA). One
  * kernel of 4 CTAs of 256 threads per SM runs 8 independent chains of
- * 4 * iters FMAs per thread; after one warm-up launch, the best of `reps`
+ * 4 * iters FMAs per thread, scalar (packed = 0) or packed FP32x2 FMAs
+ * (packed = 1, 4 flop each); after one warm-up launch, the best of `reps`
  * launches timed with CUDA events on `stream` gives *tflops_host (2 flop per
  * FMA) and *ms_host (may be NULL). iters in [1, 2^24], reps in [1, 1000],
  * else BF_EINVAL. Synchronises `stream`. */
-bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *tflops_host, double *ms_host, void *stream);
+bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, int32_t packed, double *tflops_host, double *ms_host,
+                               void *stream);
 
 /* Number of product kernels (or graph replays) this plan has launched so far
  * (0 for a NULL plan). */

@@ -83,6 +83,45 @@ bf_status bf_filter_apply_host(bf_filter filter, const void *s_host, int64_t n_s
  * path always orders its own copies. BF_EINVAL unless independent is 0 or 1. */
 bf_status bf_filter_set_s_independent(bf_filter filter, int32_t independent);
 
+/* ------------------------------------------------------------------ building blocks
+ * The paper's optimizer picks, per size and target, the best building block
+ * for an operation (Sec. IV). The filter has these blocks (variants):
+ *   0 : two passes per transform (2048 = 64 x 32), one warp per block of
+ *       samples, 11 warps per CTA (the default)
+ *   1, 2, 3 : the same kernel with 10, 8 or 6 warps per CTA
+ *   4 : three passes per transform (2048 = 16 x 16 x 8), 128 threads per
+ *       block, 4 blocks per CTA, the next block prefetched into shared memory
+ *   5 : the two-pass kernel with 12 warps per CTA, the spectrum read through
+ *       L1 instead of shared memory
+ * Variants 0 to 3 and 5 give bit-identical results; variant 4 rounds
+ * differently (another factorisation) within the same accuracy. The spectrum
+ * of the taps is always computed the same way, whatever the variant. */
+
+/* Select the variant used by bf_filter_apply and bf_filter_apply_host
+ * (BF_EINVAL outside [0, 6)). */
+bf_status bf_filter_set_variant(bf_filter filter, int32_t variant);
+
+/* The variant in use (-1 for a NULL filter). */
+int32_t bf_filter_get_variant(bf_filter filter);
+
+/* Time every variant on this GPU on n_sig synthetic blocks (1 <= n_sig <=
+ * 2^20; scratch of 2 x n_sig x 16 KB is allocated and freed here; the best
+ * of 3 rounds of 10 back-to-back launches) and select the fastest of the
+ * bit-identical variants 0 to 3 and 5 (so tuning never changes a result bit).
+ * Runs on `stream` and synchronises it. BF_ENOTFOUND if no taps are set. */
+bf_status bf_filter_autotune(bf_filter filter, int64_t n_sig, void *stream);
+
+/* The tuned time of a variant in microseconds per launch (0 if not timed)
+ * and the n_sig it was timed on. Either pointer may be NULL. */
+bf_status bf_filter_tune_query(bf_filter filter, int32_t variant, double *us_per_launch, int64_t *n_sig);
+
+/* Save / load the filter's choice and timings as JSON ("libbf-tune-2",
+ * "kind": "filter") with the target it was measured on (device name,
+ * compute capability, SM count). bf_filter_tune_load refuses (BF_EINVAL,
+ * the filter unchanged) a table from another target or of another kind. */
+bf_status bf_filter_tune_save(bf_filter filter, const char *path);
+bf_status bf_filter_tune_load(bf_filter filter, const char *path);
+
 /* Number of kernel launches issued by this filter so far. */
 int64_t bf_filter_launch_count(bf_filter filter);
 

@@ -350,6 +350,12 @@ def _filter_sigs(L):
             "bf_filter_apply_host": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
             "bf_filter_launch_count": (c_int64, [c_void_p]),
             "bf_filter_set_s_independent": (c_int, [c_void_p, c_int32]),
+            "bf_filter_set_variant": (c_int, [c_void_p, c_int32]),
+            "bf_filter_get_variant": (c_int32, [c_void_p]),
+            "bf_filter_autotune": (c_int, [c_void_p, c_int64, c_void_p]),
+            "bf_filter_tune_query": (c_int, [c_void_p, c_int32, POINTER(c_double), POINTER(c_int64)]),
+            "bf_filter_tune_save": (c_int, [c_void_p, c_char_p]),
+            "bf_filter_tune_load": (c_int, [c_void_p, c_char_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -398,6 +404,40 @@ def bf_filter_apply_host(filt, s_host, n_sig: int, y_host, stream=None) -> None:
 def bf_filter_set_s_independent(filt, independent: bool = True) -> None:
     """Declare that no pending launch of the library writes the s of later calls (see bf_filter.h)."""
     _fcheck(_filter_sigs(lib()).bf_filter_set_s_independent(filt, 1 if independent else 0), filt)
+
+
+FILTER_VARIANTS = {0: "two-pass, 11 warps per CTA", 1: "two-pass, 10 warps per CTA", 2: "two-pass, 8 warps per CTA",
+                   3: "two-pass, 6 warps per CTA", 4: "three-pass, 4 teams of 128 threads per CTA",
+                   5: "two-pass, 12 warps per CTA, spectrum through L1"}
+
+
+def bf_filter_set_variant(filt, variant: int) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_set_variant(filt, int(variant)), filt)
+
+
+def bf_filter_get_variant(filt) -> int:
+    return int(_filter_sigs(lib()).bf_filter_get_variant(filt))
+
+
+def bf_filter_autotune(filt, n_sig: int, stream=None) -> int:
+    """Time every variant on n_sig blocks, select the fastest bit-identical one; returns it."""
+    _fcheck(_filter_sigs(lib()).bf_filter_autotune(filt, int(n_sig), _stream(stream)), filt)
+    return bf_filter_get_variant(filt)
+
+
+def bf_filter_tune_query(filt, variant: int) -> Tuple[float, int]:
+    """(microseconds per launch, n_sig timed) of one variant (0.0 if not timed)."""
+    us, n = c_double(), c_int64()
+    _fcheck(_filter_sigs(lib()).bf_filter_tune_query(filt, int(variant), ctypes.byref(us), ctypes.byref(n)), filt)
+    return float(us.value), int(n.value)
+
+
+def bf_filter_tune_save(filt, path: str) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_tune_save(filt, path.encode()), filt)
+
+
+def bf_filter_tune_load(filt, path: str) -> None:
+    _fcheck(_filter_sigs(lib()).bf_filter_tune_load(filt, path.encode()), filt)
 
 
 def bf_filter_launch_count(filt) -> int:
@@ -480,13 +520,14 @@ def bf_errnorm_noalloc(R_dev, Rref_dev, n_blocks: int, stream=None) -> Tuple[flo
     return float(tot[0]), float(tot[1])
 
 
-def bf_measure_fp32_peak(iters: int = 20000, reps: int = 5, stream=None) -> Tuple[float, float]:
-    """(TFLOP/s, ms per launch) of the CUDA cores' FP32 FMA probe."""
+def bf_measure_fp32_peak(iters: int = 20000, reps: int = 5, packed: bool = False, stream=None) -> Tuple[float, float]:
+    """(TFLOP/s, ms per launch) of the CUDA cores' FP32 FMA probe (scalar or packed FP32x2)."""
     L = lib()
     L.bf_measure_fp32_peak.restype = c_int
-    L.bf_measure_fp32_peak.argtypes = [c_int32, c_int32, POINTER(c_double), POINTER(c_double), c_void_p]
+    L.bf_measure_fp32_peak.argtypes = [c_int32, c_int32, c_int32, POINTER(c_double), POINTER(c_double), c_void_p]
     t, ms = c_double(), c_double()
-    st = L.bf_measure_fp32_peak(int(iters), int(reps), ctypes.byref(t), ctypes.byref(ms), _stream(stream))
+    st = L.bf_measure_fp32_peak(int(iters), int(reps), int(bool(packed)), ctypes.byref(t), ctypes.byref(ms),
+                                _stream(stream))
     if st != BF_OK:
         raise BfError(st, bf_last_error(None))
     return float(t.value), float(ms.value)

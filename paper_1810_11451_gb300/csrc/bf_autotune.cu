@@ -162,7 +162,7 @@ extern "C" bf_status bf_tune_save(bf_plan plan, const char *path) {
     std::string name = plan->device_name;
     for (char &ch : name)
         if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
-    fprintf(fh, "{\n  \"format\": \"libbf-tune-2\",\n");
+    fprintf(fh, "{\n  \"format\": \"libbf-tune-2\",\n  \"kind\": \"product\",\n");
     fprintf(fh, "  \"target\": {\"device\": \"%s\", \"cc\": %d, \"sm_count\": %d},\n", name.c_str(), plan->cc,
             plan->sm_count);
     fprintf(fh, "  \"simt_ctas_per_sm\": %d,\n", T.simt_ctas_per_sm);
@@ -238,6 +238,7 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
     auto bad = [&](const char *why) { return bf_fail(plan, BF_EINVAL, "%s: %s", path, why); };
     bf_status ts = check_target(plan, path, txt, plan->device_name.c_str(), plan->cc, plan->sm_count);
     if (ts != BF_OK) return ts;
+    if (txt.find("\"kind\": \"filter\"") != std::string::npos) return bad("a filter tune table, not a product one");
     size_t pos;
     TuneTable T;
     pos = txt.find("\"simt_ctas_per_sm\":");

@@ -1,7 +1,14 @@
 // bf_filter.cu -- the fast-convolution filter y = IFFT(MULT(FFT(s))) of
-// Sec. III (filter equation, Fig. 4), N = 2048, FP32, one fused kernel.
+// Sec. III (filter equation, Fig. 4), N = 2048, FP32, one fused kernel per
+// call. Two kernels implement it (building blocks chosen per size and GPU by
+// bf_filter_autotune, Sec. IV):
+//  - bf_filter_warp_kernel (the default; see its own comment further down):
+//    one warp per block of samples, two Stockham passes per transform
+//    (2048 = 64 x 32), the block crossing shared memory once per transform;
+//  - bf_filter_kernel, described here: three passes per transform.
 //
-// A team of 128 threads filters one block of 2048 samples; each thread holds
+// Three-pass form. A team of 128 threads filters one block of 2048 samples;
+// each thread holds
 // 16 complex values in registers. Both transforms are Stockham passes of
 // radix 16, 16 and 8 (2048 = 16 * 16 * 8): a pass reads the R values
 // x[j + m N/R] of butterfly j, multiplies them by e^{-+2 pi i m k / (Ns R)},
@@ -29,6 +36,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -333,6 +341,257 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two-pass form: one warp per block, 2048 = 64 x 32.
+//
+// Each transform is two Stockham passes instead of three, and the block
+// stays in one exchange buffer E per warp (no barrier but __syncwarp):
+//  - forward pass A (radix 64, Ns = 1): lane l is butterfly j = l, holds
+//    x[j + 32 m], m < 64, and writes its 64-point DFT to row j of E,
+//    E[64 j + q];
+//  - forward pass B (radix 32, Ns = 64): butterflies j = l and l + 32, one at
+//    a time, read column j, E[j + 64 m], m < 32, twist by e^{-2 pi i j m / N}
+//    and give X[j + 64 q]; the product with H / N follows in registers;
+//  - inverse pass B' (radix 32, Ns = 1) takes exactly those values, and its
+//    output (j, q) goes back to the place it came from, E[j + 64 q], so each
+//    of the two butterflies of a lane touches only its own column;
+//  - inverse pass A' (radix 64, Ns = 32): butterfly j = l needs inverse
+//    values (m, j), m < 64, which is row j of E; it twists them by
+//    e^{+2 pi i j m / N} and stores y[j + 32 q], coalesced.
+// Both transforms run the forward DFT code: the inverse DFT of z is the
+// conjugate of the forward DFT of conj(z). So the product writes
+// conj(X H / N) (conjugation folded into the multiply), E holds conjugated
+// inverse values, pass A' twists them by the forward twiddles, and y is the
+// conjugate of its last DFT. The 64- and 32-point DFTs run in registers as
+// 8 x 8 and 8 x 4 splits with constant twiddles, each once in the code (two
+// loops of two rounds), so the loop body stays small. The pass twiddles come
+// from a 64 x 32 table e^{-2 pi i a b / N} (row stride 33); E has one pad per
+// 64 values, so every access of a half-warp touches 16 distinct 8-byte bank
+// pairs. The next block is copied into E (unpadded) with cp.async while the
+// current one finishes its last pass.
+constexpr int XBUF = N + N / 64;               // exchange buffer per warp
+constexpr int TB_ROW = 33;
+constexpr int TB_SIZE = 64 * TB_ROW;           // e^{-2 pi i a b / N}, a < 64, b < 32, at a * 33 + b
+// shared memory of a CTA of `warps` warps (blocks in flight), one CTA per SM;
+// with hg the spectrum is read from global memory (through L1) instead of
+// shared memory, which leaves room for more warps
+__host__ __device__ constexpr int wsmem_bytes(int warps, bool hg = false) {
+    return (TB_SIZE + (hg ? 0 : N) + warps * XBUF) * 8;
+}
+static_assert(wsmem_bytes(11) <= 232448, "11 warps per CTA exceed the shared memory of one SM");
+static_assert(wsmem_bytes(12, true) <= 232448, "12 warps per CTA exceed the shared memory of one SM");
+
+__host__ __device__ constexpr int padf(int e) { return e + (e >> 6); }
+
+// cos(2 pi k / 64) for k in [0, 16]
+__device__ __forceinline__ float cos64(int k) {
+    switch (k) {
+        case 1: return 0.99518472667219693f;
+        case 2: return 0.98078528040323043f;
+        case 3: return 0.95694033573220882f;
+        case 4: return 0.92387953251128674f;
+        case 5: return 0.88192126434835505f;
+        case 6: return 0.83146961230254524f;
+        case 7: return 0.77301045336273699f;
+        case 8: return 0.70710678118654757f;
+        case 9: return 0.63439328416364549f;
+        case 10: return 0.55557023301960229f;
+        case 11: return 0.47139673682599781f;
+        case 12: return 0.38268343236508984f;
+        case 13: return 0.29028467725446233f;
+        case 14: return 0.19509032201612833f;
+        case 15: return 0.09801714032956077f;
+        case 16: return 0.f;
+        default: return 1.f;
+    }
+}
+
+// a * e^{-2 pi i n / 64} for a constant n (after unrolling): quarter turns and
+// odd multiples of an eighth turn take their exact short forms.
+__device__ __forceinline__ float2 twc(float2 a, int n) {
+    n &= 63;
+    const int quad = n >> 4, k = n & 15;
+    float2 r;
+    if (k == 0) {
+        r = a;
+    } else if (k == 8) {
+        r = make_float2((a.x + a.y) * R2, (a.y - a.x) * R2);
+    } else {
+        const float c = cos64(k), sn = cos64(16 - k);
+        r = make_float2(fmaf(a.x, c, a.y * sn), fmaf(-a.x, sn, a.y * c));
+    }
+    if (quad == 1) return cmul_i<-1>(r);
+    if (quad == 2) return make_float2(-r.x, -r.y);
+    if (quad == 3) return cmul_i<1>(r);
+    return r;
+}
+
+// conj(a * b) with the conjugation folded into the multiply
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(-a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float conj_im(float x) { return __int_as_float(__float_as_int(x) ^ 0x80000000); }
+
+// forward 8-point DFT of v[b + s i], i < 8, in place, natural order
+template <int L>
+__device__ __forceinline__ void dft8_at(float2 (&v)[L], int b, int s) {
+    float2 u[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = v[b + s * i];
+    dft8<-1>(u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[b + s * i] = u[i];
+}
+
+// forward 64-point DFT of v[m] (natural order); X[q1 + 8 q2] ends at v[8 q1 + q2]
+__host__ __device__ constexpr int pos64(int q) { return 8 * (q & 7) + (q >> 3); }
+__device__ __forceinline__ void dft64(float2 (&v)[64]) {
+#pragma unroll
+    for (int m2 = 0; m2 < 8; ++m2) dft8_at(v, m2, 8);
+#pragma unroll
+    for (int m2 = 1; m2 < 8; ++m2)
+#pragma unroll
+        for (int q1 = 1; q1 < 8; ++q1) v[m2 + 8 * q1] = twc(v[m2 + 8 * q1], m2 * q1);
+#pragma unroll
+    for (int q1 = 0; q1 < 8; ++q1) dft8_at(v, 8 * q1, 1);
+}
+
+// forward 32-point DFT of v[m] (natural order); X[q1 + 8 q2] ends at v[4 q1 + q2]
+__host__ __device__ constexpr int pos32(int q) { return 4 * (q & 7) + (q >> 3); }
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2) dft8_at(v, m2, 4);
+#pragma unroll
+    for (int m2 = 1; m2 < 4; ++m2)
+#pragma unroll
+        for (int q1 = 1; q1 < 8; ++q1) v[m2 + 4 * q1] = twc(v[m2 + 4 * q1], 2 * m2 * q1);
+#pragma unroll
+    for (int q1 = 0; q1 < 8; ++q1) dft4<-1>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+}
+
+// The warp's copy of one block (16 KB) into E, unpadded: 32 asynchronous
+// 16-byte copies per lane, one commit group.
+__device__ __forceinline__ void stage_block(float2 *dst, const float2 *src, int l) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int off = (l + 32 * i) * 16;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + off), "l"(g + off) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// FILTER: y = IFFT(Hs * FFT(s)) with Hs = FFT(h) / N; else y = FFT(s). The
+// launch ordering is that of bf_filter_kernel (programmatic stream
+// serialization; s read after the previous launch completes unless s_indep,
+// y always written after it).
+// HG: H / N is read from global memory (Hn_g, through L1), not shared memory.
+template <bool FILTER, int WARPS, bool HG = false>
+__global__ void __launch_bounds__(32 * WARPS, 1)
+    bf_filter_warp_kernel(const float2 *s, float2 *y, long long n_sig, const float2 *__restrict__ tb_g,
+                          const float2 *__restrict__ H_g, int s_indep, const float2 *__restrict__ Hn_g) {
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *TB = sm;
+    float2 *Hs = sm + TB_SIZE;  // H / N (not HG)
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float2 *E = sm + TB_SIZE + (HG ? 0 : N) + warp * XBUF;
+    for (int i = threadIdx.x; i < (HG ? 0 : N) + TB_SIZE; i += 32 * WARPS) {
+        if (i < TB_SIZE) {
+            TB[i] = tb_g[i];
+        } else if (FILTER) {
+            const float2 h = H_g[i - TB_SIZE];
+            Hs[i - TB_SIZE] = make_float2(h.x * (1.f / N), h.y * (1.f / N));
+        }
+    }
+    __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    bool dep_done = false;
+    if (!s_indep) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        dep_done = true;
+    }
+    const long long stride = (long long)gridDim.x * WARPS;
+    long long q = (long long)blockIdx.x * WARPS + warp;
+    if (q < n_sig) stage_block(E, s + q * N, l);
+    for (; q < n_sig; q += stride) {
+        float2 v[64];
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 64; ++m) v[m] = E[l + 32 * m];
+        __syncwarp();  // every lane has its inputs before E is overwritten
+        // Round 0: forward pass A. Round 1: inverse pass A' (conjugated).
+#pragma unroll 1
+        for (int round = 0;; ++round) {
+            dft64(v);
+            if (round == 1 || !FILTER) break;
+#pragma unroll
+            for (int q2 = 0; q2 < 64; ++q2) E[padf(64 * l + q2)] = v[pos64(q2)];
+            __syncwarp();
+            // forward pass B, product, inverse pass B' for the lane's two columns
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int j = l + 32 * h;
+                float2 u[32];
+                u[0] = E[padf(j)];
+#pragma unroll
+                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
+#pragma unroll 1
+                for (int sub = 0;; ++sub) {
+                    dft32(u);
+                    if (sub == 1) break;
+                    float2 t[32];
+#pragma unroll
+                    for (int m = 0; m < 32; ++m)
+                        t[m] = cmul_conj(u[pos32(m)], HG ? __ldg(Hn_g + j + 64 * m) : Hs[j + 64 * m]);
+#pragma unroll
+                    for (int m = 0; m < 32; ++m) u[m] = t[m];
+                }
+#pragma unroll
+                for (int q2 = 0; q2 < 32; ++q2) E[padf(j + 64 * q2)] = u[pos32(q2)];
+            }
+            __syncwarp();
+            // inverse pass A' input: row l of E (conjugated values), forward twiddles
+            v[0] = E[padf(64 * l)];
+#pragma unroll
+            for (int m = 1; m < 64; ++m) v[m] = cmul(E[padf(64 * l + m)], TB[m * TB_ROW + l]);
+            __syncwarp();  // E is free: copy the next block in while this one finishes
+            if (q + stride < n_sig) stage_block(E, s + (q + stride) * N, l);
+        }
+        if (!dep_done) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            dep_done = true;
+        }
+        float2 *yq = y + q * N;
+        if (FILTER) {
+#pragma unroll
+            for (int q2 = 0; q2 < 64; ++q2) {
+                const float2 r = v[pos64(q2)];
+                yq[l + 32 * q2] = make_float2(r.x, conj_im(r.y));
+            }
+        } else {  // spectrum: pass B alone, X[j + 64 q]
+#pragma unroll
+            for (int q2 = 0; q2 < 64; ++q2) E[padf(64 * l + q2)] = v[pos64(q2)];
+            __syncwarp();
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int j = l + 32 * h;
+                float2 u[32];
+                u[0] = E[padf(j)];
+#pragma unroll
+                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
+                dft32(u);
+#pragma unroll
+                for (int q2 = 0; q2 < 32; ++q2) yq[j + 64 * q2] = u[pos32(q2)];
+            }
+            __syncwarp();
+            if (q + stride < n_sig) stage_block(E, s + (q + stride) * N, l);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 }  // namespace bff
 
 using namespace bff;
@@ -340,6 +599,8 @@ using namespace bff;
 struct bf_filter_s {
     int device = 0, sm_count = 0;
     float2 *tw = nullptr, *H = nullptr, *hpad = nullptr;
+    float2 *tb = nullptr;  // pass twiddles of the two-pass form, e^{-2 pi i a b / N} at a * 33 + b
+    float2 *Hn = nullptr;  // H / N (the spectrum scaled once, for the variant that reads it from global memory)
     bool has_taps = false;
     std::string err;
     int64_t launches = 0;
@@ -351,6 +612,11 @@ struct bf_filter_s {
     size_t slot_cap = 0;  // blocks per slot
     int slot_next = 0;    // next slot (the ring continues across calls)
     bool s_indep = false; // bf_filter_set_s_independent
+    int variant = 0;      // bf_filter_set_variant
+    double tuned_us[6] = {};  // bf_filter_autotune: microseconds per launch of each variant (0: not timed)
+    int64_t tuned_n_sig = 0;
+    std::string device_name;
+    int cc = 0;
 };
 
 static thread_local std::string g_create_err;
@@ -384,15 +650,59 @@ static bf_status ff_device(bf_filter f) {
 // Filter launches may start while the previous kernel on the stream finishes
 // (see bf_filter_kernel); the spectrum launch releases its dependents only by
 // completing, so a filter launch never reads a spectrum still being written.
+// Hn = H / N (1/N is a power of two: exact)
+__global__ void bf_scale_spectrum_kernel(const float2 *H, float2 *Hn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float2 h = H[i];
+    Hn[i] = make_float2(h.x * (1.f / N), h.y * (1.f / N));
+}
+
+// The building blocks a filter can run (bf_filter_set_variant): the two-pass
+// kernel with 11, 10, 8 or 6 warps per CTA, or 12 with the spectrum read
+// through L1 (bit-identical results), and the three-pass kernel with four
+// 128-thread teams per CTA.
+constexpr int N_VARIANTS = 6;
+
+template <bool FILTER, int WARPS, bool HG = false>
+static cudaError_t launch_warp(const float2 *s, float2 *y, long long n_sig, const bf_filter f, cudaStream_t st,
+                               bool s_indep) {
+    const long long want = (n_sig + WARPS - 1) / WARPS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(want, (long long)f->sm_count));
+    cfg.blockDim = dim3(32 * WARPS);
+    cfg.dynamicSmemBytes = wsmem_bytes(WARPS, HG);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = FILTER ? 1 : 0;  // the spectrum launch waits for everything before it
+    return cudaLaunchKernelEx(&cfg, bf_filter_warp_kernel<FILTER, WARPS, HG>, s, y, n_sig, (const float2 *)f->tb,
+                              (const float2 *)(FILTER ? f->H : nullptr), s_indep ? 1 : 0, (const float2 *)f->Hn);
+}
+
+template <bool FILTER, int WARPS, bool HG = false>
+static cudaError_t configure_warp() {
+    return cudaFuncSetAttribute(bf_filter_warp_kernel<FILTER, WARPS, HG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                wsmem_bytes(WARPS, HG));
+}
+
+// filter = false: y = FFT(s), always by the two-pass kernel, so the spectrum
+// of the taps is the same whatever variant filters the blocks.
 static cudaError_t launch_filter(bool filter, const float2 *s, float2 *y, long long n_sig, const bf_filter f,
-                                 cudaStream_t st, bool s_indep = false) {
+                                 cudaStream_t st, bool s_indep = false, int variant = -1) {
     if (n_sig <= 0) return cudaSuccess;
+    if (!filter) return launch_warp<false, 11>(s, y, n_sig, f, st, false);
+    switch (variant < 0 ? f->variant : variant) {
+        case 1: return launch_warp<true, 10>(s, y, n_sig, f, st, s_indep);
+        case 2: return launch_warp<true, 8>(s, y, n_sig, f, st, s_indep);
+        case 3: return launch_warp<true, 6>(s, y, n_sig, f, st, s_indep);
+        case 5: return launch_warp<true, 12, true>(s, y, n_sig, f, st, s_indep);
+        case 4: break;
+        default: return launch_warp<true, 11>(s, y, n_sig, f, st, s_indep);
+    }
     const long long want = (n_sig + TEAMS - 1) / TEAMS;
     const int grid = (int)std::min<long long>(want, (long long)f->sm_count * CTAS_PER_SM);
-    if (!filter) {
-        bf_filter_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(s, y, n_sig, f->tw, nullptr, 0);
-        return cudaGetLastError();
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(THREADS);
@@ -422,6 +732,8 @@ extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
     bf_filter f = new bf_filter_s();
     f->device = dev;
     f->sm_count = prop.multiProcessorCount;
+    f->device_name = prop.name;
+    f->cc = prop.major * 10 + prop.minor;
     // per-pass twiddles e^{-2 pi i e / N}, from FP64 values rounded once to FP32
     std::vector<float2> tw(N, make_float2(0.f, 0.f));
     auto root = [](int e) {
@@ -433,13 +745,20 @@ extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
         tw[16 + k] = root(32 * k);  // e^{-2 pi i 4 k / 256}
     }
     for (int j = 0; j < 256; ++j) tw[TW3 + j] = root(j);  // e^{-2 pi i j / 2048}
+    std::vector<float2> tb(TB_SIZE, make_float2(0.f, 0.f));
+    for (int a = 0; a < 64; ++a)
+        for (int b = 0; b < 32; ++b) tb[a * TB_ROW + b] = root(a * b);  // e^{-2 pi i a b / 2048}
     bool ok = cudaMalloc((void **)&f->tw, N * sizeof(float2)) == cudaSuccess &&
               cudaMalloc((void **)&f->H, N * sizeof(float2)) == cudaSuccess &&
               cudaMalloc((void **)&f->hpad, N * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc((void **)&f->tb, TB_SIZE * sizeof(float2)) == cudaSuccess &&
               cudaMemcpy(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(f->tb, tb.data(), TB_SIZE * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+              configure_warp<false, 11>() == cudaSuccess && configure_warp<true, 11>() == cudaSuccess &&
+              configure_warp<true, 10>() == cudaSuccess && configure_warp<true, 8>() == cudaSuccess &&
+              configure_warp<true, 6>() == cudaSuccess && configure_warp<true, 12, true>() == cudaSuccess &&
+              cudaMalloc((void **)&f->Hn, N * sizeof(float2)) == cudaSuccess &&
               cudaFuncSetAttribute(bf_filter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   SMEM_BYTES) == cudaSuccess &&
-              cudaFuncSetAttribute(bf_filter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES) == cudaSuccess &&
               cudaStreamCreateWithFlags(&f->x_in, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&f->x_run, cudaStreamNonBlocking) == cudaSuccess &&
@@ -464,7 +783,7 @@ extern "C" bf_status bf_filter_destroy(bf_filter f) {
     cudaSetDevice(f->device);
     cudaDeviceSynchronize();
     cudaGetLastError();
-    for (void *p : {(void *)f->tw, (void *)f->H, (void *)f->hpad})
+    for (void *p : {(void *)f->tw, (void *)f->H, (void *)f->hpad, (void *)f->tb, (void *)f->Hn})
         if (p) cudaFree(p);
     for (int i = 0; i < 3; ++i) {
         if (f->slot_s[i]) cudaFree(f->slot_s[i]);
@@ -496,6 +815,9 @@ extern "C" bf_status bf_filter_set_taps(bf_filter f, const void *h_dev, int n_ta
     FF_CK(f, cudaMemsetAsync(f->hpad, 0, N * sizeof(float2), st));
     FF_CK(f, cudaMemcpyAsync(f->hpad, h_dev, (size_t)n_taps * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     FF_CK(f, launch_filter(false, f->hpad, f->H, 1, f, st));
+    f->launches++;
+    bf_scale_spectrum_kernel<<<N / 256, 256, 0, st>>>(f->H, f->Hn);
+    FF_CK(f, cudaGetLastError());
     f->launches++;
     f->has_taps = true;
     return BF_OK;
@@ -597,5 +919,136 @@ extern "C" bf_status bf_filter_apply_host(bf_filter f, const void *s_host, int64
     }
     FF_CK(f, cudaEventRecord(f->x_end, f->x_out));
     FF_CK(f, cudaStreamWaitEvent(user, f->x_end, 0));
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ building blocks and their tuning
+
+extern "C" bf_status bf_filter_set_variant(bf_filter f, int32_t variant) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (variant < 0 || variant >= N_VARIANTS)
+        return ff_fail(f, BF_EINVAL, "variant %d is outside [0, %d)", variant, N_VARIANTS);
+    f->variant = variant;
+    return BF_OK;
+}
+
+extern "C" int32_t bf_filter_get_variant(bf_filter f) { return f ? f->variant : -1; }
+
+// Times every variant on n_sig synthetic blocks (scratch allocated and freed
+// here) and keeps the fastest of the bit-identical two-pass variants.
+extern "C" bf_status bf_filter_autotune(bf_filter f, int64_t n_sig, void *stream) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (n_sig < 1 || n_sig > (1 << 20)) return ff_fail(f, BF_EINVAL, "n_sig = %lld is outside [1, 2^20]",
+                                                       (long long)n_sig);
+    if (!f->has_taps) return ff_fail(f, BF_ENOTFOUND, "no filter sequence set");
+    bf_status st = ff_device(f);
+    if (st != BF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n_sig * N * sizeof(float2);
+    float2 *a = nullptr, *b = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&] {
+        if (a) cudaFree(a);
+        if (b) cudaFree(b);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaGetLastError();
+    };
+    if (cudaMalloc((void **)&a, bytes) != cudaSuccess || cudaMalloc((void **)&b, bytes) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return ff_fail(f, BF_ENOMEM, "autotune scratch (%zu bytes twice) could not be allocated", bytes);
+    }
+    double us[N_VARIANTS] = {};
+    cudaError_t e = cudaMemsetAsync(a, 0x3C, bytes, s);  // finite values (about 0.0115 as FP32)
+    constexpr int WARM = 3, REPS = 10, ROUNDS = 3;
+    for (int v = 0; v < N_VARIANTS && e == cudaSuccess; ++v) {
+        double best = 0.0;
+        for (int r = 0; r < ROUNDS && e == cudaSuccess; ++r) {
+            for (int i = 0; i < WARM && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, false, v);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int i = 0; i < REPS && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, false, v);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            const double t = ms * 1e3 / REPS;
+            if (e == cudaSuccess && (r == 0 || t < best)) best = t;
+        }
+        f->launches += ROUNDS * (WARM + REPS);
+        us[v] = best;
+    }
+    cleanup();
+    if (e != cudaSuccess) return ff_fail(f, BF_ECUDA, "filter autotune: %s", cudaGetErrorString(e));
+    int pick = 0;
+    for (int v = 1; v < N_VARIANTS; ++v)
+        if (v != 4 && us[v] < us[pick]) pick = v;  // variant 4 rounds differently
+    for (int v = 0; v < N_VARIANTS; ++v) f->tuned_us[v] = us[v];
+    f->tuned_n_sig = n_sig;
+    f->variant = pick;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_tune_query(bf_filter f, int32_t variant, double *us_per_launch, int64_t *n_sig) {
+    if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
+    if (variant < 0 || variant >= N_VARIANTS) return ff_fail(f, BF_EINVAL, "variant %d is out of range", variant);
+    if (us_per_launch) *us_per_launch = f->tuned_us[variant];
+    if (n_sig) *n_sig = f->tuned_n_sig;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_filter_tune_save(bf_filter f, const char *path) {
+    if (!f || !path) return ff_fail(f, BF_EINVAL, "NULL argument");
+    FILE *fh = fopen(path, "w");
+    if (!fh) return ff_fail(f, BF_EINVAL, "cannot open %s for writing", path);
+    std::string name = f->device_name;
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+    fprintf(fh, "{\n  \"format\": \"libbf-tune-2\",\n  \"kind\": \"filter\",\n");
+    fprintf(fh, "  \"target\": {\"device\": \"%s\", \"cc\": %d, \"sm_count\": %d},\n", name.c_str(), f->cc,
+            f->sm_count);
+    fprintf(fh, "  \"n\": %d,\n  \"n_sig\": %lld,\n  \"variant\": %d,\n  \"us_per_launch\": [", N,
+            (long long)f->tuned_n_sig, f->variant);
+    for (int v = 0; v < N_VARIANTS; ++v) fprintf(fh, "%s%.4f", v ? ", " : "", f->tuned_us[v]);
+    fprintf(fh, "]\n}\n");
+    return fclose(fh) == 0 ? BF_OK : ff_fail(f, BF_EINVAL, "write to %s failed", path);
+}
+
+extern "C" bf_status bf_filter_tune_load(bf_filter f, const char *path) {
+    if (!f || !path) return ff_fail(f, BF_EINVAL, "NULL argument");
+    if (bf_tune_check_target(path, f->device_name.c_str(), f->cc, f->sm_count) != BF_OK)
+        return ff_fail(f, BF_EINVAL, "%s", bf_last_error(nullptr));
+    FILE *fh = fopen(path, "r");
+    if (!fh) return ff_fail(f, BF_EINVAL, "cannot open %s", path);
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, fh)) > 0) txt.append(buf, n);
+    fclose(fh);
+    auto bad = [&](const char *why) { return ff_fail(f, BF_EINVAL, "%s: %s", path, why); };
+    if (txt.find("\"kind\": \"filter\"") == std::string::npos) return bad("not a filter tune table");
+    int nn = 0, variant = -1;
+    long long ns = 0;
+    size_t p = txt.find("\"n\":");
+    if (p == std::string::npos || sscanf(txt.c_str() + p + 4, "%d", &nn) != 1 || nn != N) return bad("n");
+    p = txt.find("\"n_sig\":");
+    if (p == std::string::npos || sscanf(txt.c_str() + p + 8, "%lld", &ns) != 1 || ns < 0) return bad("n_sig");
+    p = txt.find("\"variant\":");
+    if (p == std::string::npos || sscanf(txt.c_str() + p + 10, "%d", &variant) != 1 || variant < 0 ||
+        variant >= N_VARIANTS)
+        return bad("variant");
+    p = txt.find("\"us_per_launch\": [");
+    if (p == std::string::npos) return bad("us_per_launch");
+    double us[N_VARIANTS];
+    const char *c = txt.c_str() + p + 18;
+    for (int v = 0; v < N_VARIANTS; ++v) {
+        char *end = nullptr;
+        us[v] = strtod(c, &end);
+        if (end == c || us[v] < 0) return bad("us_per_launch value");
+        c = end + (*end == ',' ? 1 : 0);
+    }
+    f->variant = variant;
+    f->tuned_n_sig = ns;
+    for (int v = 0; v < N_VARIANTS; ++v) f->tuned_us[v] = us[v];
     return BF_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bf.h"
 #include "bf_plan.h"
@@ -16,33 +17,46 @@ constexpr int THREADS = 256;
 constexpr int CTAS_PER_SM = 4;
 
 // Every thread runs CHAINS independent chains a <- a * b + c for `iters`
-// rounds: 2 * CHAINS * iters flop per thread, no memory traffic inside the
-// loop. b is just below 1 and c small, so the values stay finite and normal.
-// The final store is conditional on a value no chain reaches, so the compiler
-// cannot drop the loop, and it never writes in practice.
+// rounds of 4: 2 * 4 * CHAINS * iters flop per thread (twice that with packed
+// FP32x2 FMAs, PACKED), no memory traffic inside the loop. b is just below 1
+// and c small, so the values stay finite and normal. The final store is
+// conditional on a value no chain reaches, so the compiler cannot drop the
+// loop, and it never writes in practice.
+template <bool PACKED>
 __global__ void __launch_bounds__(THREADS) bf_ffma_peak_kernel(float *sink, int iters, float b, float c) {
-    float a[CHAINS];
+    using V = typename std::conditional<PACKED, float2, float>::type;
+    V a[CHAINS];
 #pragma unroll
-    for (int k = 0; k < CHAINS; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int k = 0; k < CHAINS; ++k) {
+        const float x = (float)(threadIdx.x + k) * 1e-3f;
+        if constexpr (PACKED) a[k] = make_float2(x, x + 0.5f);
+        else a[k] = x;
+    }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int k = 0; k < CHAINS; ++k) a[k] = __fmaf_rn(a[k], b, c);
+            for (int k = 0; k < CHAINS; ++k) {
+                if constexpr (PACKED) a[k] = __ffma2_rn(a[k], make_float2(b, b), make_float2(c, c));
+                else a[k] = __fmaf_rn(a[k], b, c);
+            }
     }
     float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < CHAINS; ++k) s += a[k];
+    for (int k = 0; k < CHAINS; ++k) {
+        if constexpr (PACKED) s += a[k].x + a[k].y;
+        else s += a[k];
+    }
     if (s == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
 
-extern "C" bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *tflops_host, double *ms_host,
-                                          void *stream) {
-    if (!tflops_host || iters < 1 || iters > (1 << 24) || reps < 1 || reps > 1000)
+extern "C" bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, int32_t packed, double *tflops_host,
+                                          double *ms_host, void *stream) {
+    if (!tflops_host || iters < 1 || iters > (1 << 24) || reps < 1 || reps > 1000 || (packed != 0 && packed != 1))
         return bf_fail(nullptr, BF_EINVAL, "bf_measure_fp32_peak: iters in [1, 2^24], reps in [1, 1000], "
-                                           "tflops_host not NULL");
+                                           "packed 0 or 1, tflops_host not NULL");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -61,7 +75,10 @@ extern "C" bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *t
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         e = cudaEventRecord(e0, s);
         if (e != cudaSuccess) break;
-        bf_ffma_peak_kernel<<<grid, THREADS, 0, s>>>(nullptr, iters, 0.9999999f, 1e-7f);
+        if (packed)
+            bf_ffma_peak_kernel<true><<<grid, THREADS, 0, s>>>(nullptr, iters, 0.9999999f, 1e-7f);
+        else
+            bf_ffma_peak_kernel<false><<<grid, THREADS, 0, s>>>(nullptr, iters, 0.9999999f, 1e-7f);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -72,7 +89,7 @@ extern "C" bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, double *t
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return bf_fail(nullptr, BF_ECUDA, "FMA probe: %s", cudaGetErrorString(e));
-    const double flop = 2.0 * CHAINS * 4 * (double)iters * (double)grid * THREADS;
+    const double flop = (packed ? 4.0 : 2.0) * CHAINS * 4 * (double)iters * (double)grid * THREADS;
     *tflops_host = flop / (best_ms * 1e-3) / 1e12;
     if (ms_host) *ms_host = best_ms;
     return BF_OK;

@@ -243,3 +243,78 @@ def test_independent_input_keeps_the_y_side_ordered(filt):
         assert bf.lib().bf_filter_set_s_independent(filt, 2) == bf.BF_EINVAL
     finally:
         bf.bf_filter_set_s_independent(filt, False)
+
+
+def test_variants_bit_identical_and_accurate(filt):
+    """The two-pass variants (11, 10, 8, 6 warps per CTA) give the same bits;
+    the three-pass variant rounds differently but every block stays within
+    the tolerance of the oracle."""
+    b = wl.config_filter_tti().rounded()  # 896 blocks
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    s_d = dev_c64(b.s)
+    outs = {}
+    try:
+        for v in range(6):
+            bf.bf_filter_set_variant(filt, v)
+            y_d = torch.full_like(s_d, float("nan"))
+            bf.bf_filter_apply(filt, s_d, b.n_sig, y_d)
+            outs[v] = host_c64(y_d).reshape(b.n_sig, N)
+        for v in (1, 2, 3, 5):
+            assert np.array_equal(outs[v].view(np.uint64), outs[0].view(np.uint64)), f"variant {v}"
+        ref = oracle.circular_filter(b.h, b.s)
+        for v in (0, 4):
+            assert_per_block(outs[v], ref, f"variant {v}")
+        with pytest.raises(bf.BfError) as ei:
+            bf.bf_filter_set_variant(filt, 6)
+        assert ei.value.status == bf.BF_EINVAL
+    finally:
+        bf.bf_filter_set_variant(filt, 0)
+
+
+def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
+    """Tuning picks the fastest of the bit-identical variants: results keep
+    every bit, the pick is no slower than the default when timed, and the
+    choice saves and loads on this GPU; a table from another target or of the
+    product kind is refused and leaves the filter unchanged."""
+    b = wl.config_filter_tti().rounded()
+    bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
+    s_d = dev_c64(b.s)
+    y0 = torch.empty_like(s_d)
+    bf.bf_filter_apply(filt, s_d, b.n_sig, y0)
+    try:
+        v = bf.bf_filter_autotune(filt, 4096)
+        assert v in (0, 1, 2, 3, 5)
+        times = {k: bf.bf_filter_tune_query(filt, k) for k in range(6)}
+        assert all(t > 0 and n == 4096 for t, n in times.values()), times
+        assert times[v][0] <= times[0][0]
+        y1 = torch.full_like(s_d, float("nan"))
+        bf.bf_filter_apply(filt, s_d, b.n_sig, y1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1.view(torch.int32), y0.view(torch.int32))
+        path = str(tmp_path / "filter_tune.json")
+        bf.bf_filter_tune_save(filt, path)
+        other = bf.bf_filter_create(N)
+        try:
+            bf.bf_filter_set_variant(other, 4)
+            bf.bf_filter_tune_load(other, path)
+            assert bf.bf_filter_get_variant(other) == v
+            assert abs(bf.bf_filter_tune_query(other, 4)[0] - times[4][0]) < 1e-3
+            txt = open(path).read()
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            bad = str(tmp_path / "other_gpu.json")
+            with open(bad, "w") as fh:
+                fh.write(txt.replace(f'"sm_count": {sms}', f'"sm_count": {sms + 8}'))
+            bf.bf_filter_set_variant(other, 4)
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_filter_tune_load(other, bad)
+            assert ei.value.status == bf.BF_EINVAL and "not on this target" in str(ei.value)
+            assert bf.bf_filter_get_variant(other) == 4
+            with open(bad, "w") as fh:
+                fh.write(txt.replace('"kind": "filter"', '"kind": "product"'))
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_filter_tune_load(other, bad)
+            assert ei.value.status == bf.BF_EINVAL
+        finally:
+            bf.bf_filter_destroy(other)
+    finally:
+        bf.bf_filter_set_variant(filt, 0)
