@@ -357,8 +357,8 @@ int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *g
  * per precoder, with tiles of 1 and of 2 blocks. It keeps the faster tile size
  * and records the marginal cost per block (the slope in ns). Later batches of
  * this precision are cut with those tile sizes and split across CTAs by those
- * costs instead of by bytes. For BF_FP32 it also picks the CTAs per SM (up to
- * as many as fit at once).
+ * costs instead of by bytes. For the two CUDA-core forms (BF_FP32, BF_FP32_3M)
+ * it also picks that form's CTAs per SM (up to as many as fit at once).
  * Allocates and frees its own scratch (about 240 MB) and runs on `stream`
  * (synchronised before return). Uses 80 precoder slots above the plan's
  * current slots, which it leaves unset. */

@@ -121,11 +121,12 @@ extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) 
         T.ns_per_block[p][b] = best_slope;
     }
     if (result == BF_OK && simt_form(prec)) {
-        // CTAs per SM of the CUDA-core kernels (shared by both forms), at f = 36
+        // CTAs per SM of this CUDA-core kernel, at f = 36
+        const int g = prec == BF_FP32_3M ? 1 : 0;
         double best = 1e30;
-        int best_c = T.simt_ctas_per_sm;
-        for (int c = 1; c <= plan->simt_resident; ++c) {
-            T.simt_ctas_per_sm = c;
+        int best_c = T.simt_ctas_per_sm[g];
+        for (int c = 1; c <= plan->simt_resident[g]; ++c) {
+            T.simt_ctas_per_sm[g] = c;
             double t2 = 0;
             if ((result = time_batch(plan, sc, prec, fs[(TUNE_BUCKETS - 1) * SLOTS_PER_F],
                                      base + (TUNE_BUCKETS - 1) * SLOTS_PER_F, n2, st, &t2)) != BF_OK)
@@ -135,7 +136,7 @@ extern "C" bf_status bf_autotune(bf_plan plan, bf_precision prec, void *stream) 
                 best_c = c;
             }
         }
-        T.simt_ctas_per_sm = best_c;
+        T.simt_ctas_per_sm[g] = best_c;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) result = bf_fail(plan, BF_ECUDA, "autotune synchronize");
     for (int i = 0; i < TUNE_BUCKETS * SLOTS_PER_F; ++i) plan->f_slot[base + i] = -1;  // release the slots
@@ -165,7 +166,7 @@ extern "C" bf_status bf_tune_save(bf_plan plan, const char *path) {
     fprintf(fh, "{\n  \"format\": \"libbf-tune-2\",\n  \"kind\": \"product\",\n");
     fprintf(fh, "  \"target\": {\"device\": \"%s\", \"cc\": %d, \"sm_count\": %d},\n", name.c_str(), plan->cc,
             plan->sm_count);
-    fprintf(fh, "  \"simt_ctas_per_sm\": %d,\n", T.simt_ctas_per_sm);
+    fprintf(fh, "  \"simt_ctas_per_sm\": [%d, %d],\n", T.simt_ctas_per_sm[0], T.simt_ctas_per_sm[1]);
     fprintf(fh, "  \"f_bucket_upper\": [0, 8, 16, 24, 36],\n  \"precisions\": [\n");
     for (int p = 0; p < N_PREC; ++p) {
         fprintf(fh, "    {\"precision\": %d, \"tuned\": %d, \"ns_per_block\": [", p, T.tuned[p] ? 1 : 0);
@@ -241,9 +242,11 @@ extern "C" bf_status bf_tune_load(bf_plan plan, const char *path) {
     if (txt.find("\"kind\": \"filter\"") != std::string::npos) return bad("a filter tune table, not a product one");
     size_t pos;
     TuneTable T;
-    pos = txt.find("\"simt_ctas_per_sm\":");
-    if (pos == std::string::npos || sscanf(txt.c_str() + pos + 19, "%d", &T.simt_ctas_per_sm) != 1 ||
-        T.simt_ctas_per_sm < 1 || T.simt_ctas_per_sm > 16)
+    pos = txt.find("\"simt_ctas_per_sm\": [");
+    if (pos == std::string::npos ||
+        sscanf(txt.c_str() + pos + 21, "%d, %d", &T.simt_ctas_per_sm[0], &T.simt_ctas_per_sm[1]) != 2 ||
+        T.simt_ctas_per_sm[0] < 1 || T.simt_ctas_per_sm[0] > 16 || T.simt_ctas_per_sm[1] < 1 ||
+        T.simt_ctas_per_sm[1] > 16)
         return bad("simt_ctas_per_sm");
     for (int p = 0; p < N_PREC; ++p) {
         char key[32];

@@ -152,8 +152,7 @@ extern "C" bf_status bf_plan_create(int n_ant, int f_max, int b, bf_plan *out) {
     p->n_ant = n_ant;
     p->f_max = f_max;
     p->b = b;
-    p->simt_resident = simt_resident_ctas();
-    p->tune.simt_ctas_per_sm = p->simt_resident;
+    for (int g = 0; g < 2; ++g) p->tune.simt_ctas_per_sm[g] = p->simt_resident[g] = simt_resident_ctas(g == 1);
     if (cudaMalloc((void **)&p->d_status, 64) != cudaSuccess || cudaMemset(p->d_status, 0, 64) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -682,7 +681,9 @@ static KParams make_params(bf_plan plan, const uint8_t *dlist, size_t tiles_byte
 }
 
 int max_cta_for(bf_plan plan, bf_precision prec) {
-    const int per_sm = simt_form(prec) ? std::max(1, std::min(plan->tune.simt_ctas_per_sm, plan->simt_resident)) : 1;
+    const int g = prec == BF_FP32_3M ? 1 : 0;
+    const int per_sm =
+        simt_form(prec) ? std::max(1, std::min(plan->tune.simt_ctas_per_sm[g], plan->simt_resident[g])) : 1;
     return plan->sm_count * per_sm;
 }
 

@@ -27,7 +27,7 @@ struct TuneTable {
     double ns_per_block[N_PREC][TUNE_BUCKETS];
     int tile_blocks[N_PREC][TUNE_BUCKETS];
     bool tuned[N_PREC] = {};
-    int simt_ctas_per_sm = 2;  // set to the resident maximum when a plan is created
+    int simt_ctas_per_sm[2] = {2, 2};  // plain, three-product form; the resident maximum at plan creation
     TuneTable() {
         for (int p = 0; p < N_PREC; ++p)
             for (int b = 0; b < TUNE_BUCKETS; ++b) {
@@ -89,7 +89,7 @@ struct bf_plan_s {
     int device = 0, sm_count = 0, n_ant = 64, f_max = 36, b = 60;
     int cc = 0;                 // compute capability, major * 10 + minor
     std::string device_name;    // cudaDeviceProp::name (the tune table's target)
-    int simt_resident = 2;  // CTAs of the CUDA-core kernels that fit on one SM (the smaller of the two)
+    int simt_resident[2] = {2, 2};  // CTAs of the CUDA-core kernels (plain, three-product) that fit on one SM
     std::string err;
     std::mutex err_mu;  // err is written from the caller's and a serving engine's threads
     // precoder store (slots)

@@ -34,7 +34,7 @@ struct KParams;
 cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream, bool three_products);
 cudaError_t launch_tc(int prec, bool held, const KParams &p, int n_cta, cudaStream_t stream);
 int simt_smem_bytes();
-int simt_resident_ctas();
+int simt_resident_ctas(bool g3m);
 int tc_smem_bytes(int prec, bool held);
 cudaError_t configure_simt();
 cudaError_t configure_tc();

@@ -317,20 +317,19 @@ cudaError_t launch_simt(const KParams &p, int n_cta, cudaStream_t stream, bool g
 
 int simt_smem_bytes() { return SimtCfg<true>::SMEM; }
 
-// CTAs of the CUDA-core kernel that fit on one SM at once (registers, shared
+// CTAs of a CUDA-core kernel that fit on one SM at once (registers, shared
 // memory, threads); a launch never asks for more than this many per SM.
-// The smaller resident count of the two CUDA-core kernels (they share one
-// CTAs-per-SM setting).
-int simt_resident_ctas() {
-    int n0 = 0, n1 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, bf_simt_kernel<false>, SIMT_THREADS,
-                                                      SimtCfg<false>::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, bf_simt_kernel<true>, SIMT_THREADS,
-                                                      SimtCfg<true>::SMEM) != cudaSuccess) {
+// g3m: the three-product form's kernel, else the plain form's.
+int simt_resident_ctas(bool g3m) {
+    int n = 0;
+    const cudaError_t e =
+        g3m ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bf_simt_kernel<true>, SIMT_THREADS, SimtCfg<true>::SMEM)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bf_simt_kernel<false>, SIMT_THREADS,
+                                                            SimtCfg<false>::SMEM);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
-    const int n = n0 < n1 ? n0 : n1;
     return n > 0 ? n : 1;
 }
 

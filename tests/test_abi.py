@@ -177,7 +177,7 @@ def _table(path, device="NVIDIA GB300", cc=103, sms=152, fmt="libbf-tune-2"):
                       f'"tile_blocks": [2, 2, 2, 2, 2]}}' for p in range(6))
     with open(path, "w") as fh:
         fh.write(f'{{\n  "format": "{fmt}",\n  "target": {{"device": "{device}", "cc": {cc}, "sm_count": {sms}}},\n'
-                 f'  "simt_ctas_per_sm": 2,\n  "f_bucket_upper": [0, 8, 16, 24, 36],\n  "precisions": [\n'
+                 f'  "simt_ctas_per_sm": [2, 2],\n  "f_bucket_upper": [0, 8, 16, 24, 36],\n  "precisions": [\n'
                  f'{prec}\n  ]\n}}\n')
 
 
