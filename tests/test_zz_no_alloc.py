@@ -5,7 +5,7 @@ which can synchronise the device and stall for an unbounded time, and some
 callers have no plan or run where another allocator owns all device memory.
 bf_errnorm_noalloc serves them: no plan, no allocation, a fixed scratch array
 inside the library. This file checks, through the C ABI, that it returns what
-the plan-based bf_errnorm returns, on two calls in a row (the second call must
+the plan-based bf_errnorm and the oracle's FP64 sums return, on two calls in a row (the second call must
 not see the first call's scratch), that a call leaves the device's free
 memory unchanged (after a first call, which may load the library's device
 code), and that it refuses batches larger than its scratch. The file is named
@@ -17,6 +17,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle  # noqa: E402
 import paper_1810_11451_gb300 as bf  # noqa: E402
 
 RTOL = 1e-12  # the tolerance the other error-norm tests use (FP64 sums in a different order)
@@ -44,6 +45,11 @@ def test_noalloc_matches_plan_errnorm_twice():
             want = bf.bf_errnorm(plan, Rd, Rrefd, n)
             got = bf.bf_errnorm_noalloc(Rd, Rrefd, n)
             assert np.allclose(got, want, rtol=RTOL, atol=0), (got, want)
+            # and against the oracle's FP64 sums of the same arrays
+            R = Rd.cpu().numpy().view(np.complex64).reshape(n, 64, 60)
+            Rref = Rrefd.cpu().numpy().view(np.complex128).reshape(n, 64, 60)
+            onum, oden = oracle.errnorm_blocks(R, Rref)
+            assert np.allclose(got, (onum.sum(), oden.sum()), rtol=RTOL, atol=0), (got, onum.sum(), oden.sum())
         assert bf.bf_errnorm_noalloc(Rd, Rrefd, 0) == (0.0, 0.0)
         # the promise itself: with the module loaded, a call takes no device memory
         torch.cuda.synchronize()
