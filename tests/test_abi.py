@@ -199,3 +199,31 @@ def test_tune_table_is_keyed_by_target(bf, tmp_path):
     assert ei.value.status == bf.BF_EINVAL
     with pytest.raises(bf.BfError):
         bf.bf_tune_check_target(str(tmp_path / "missing.json"), "NVIDIA GB300", 103, 152)
+
+
+def test_new_entry_points_reject_bad_arguments_before_cuda(bf):
+    """Argument checks that come before any CUDA call: the FMA probe's ranges,
+    the filter calls on a NULL filter, the target check's NULL arguments."""
+    L = bf.lib()
+    L.bf_measure_fp32_peak.restype = ctypes.c_int
+    L.bf_measure_fp32_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p]
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    for iters, reps, packed in [(0, 5, 0), (1 << 25, 5, 0), (10, 0, 0), (10, 1001, 0), (10, 5, 2)]:
+        assert L.bf_measure_fp32_peak(iters, reps, packed, ctypes.byref(t), ctypes.byref(ms), None) == bf.BF_EINVAL
+    assert L.bf_measure_fp32_peak(10, 5, 0, None, None, None) == bf.BF_EINVAL
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_filter_set_variant(None, 0)
+    assert ei.value.status == bf.BF_EINVAL
+    assert bf.bf_filter_get_variant(None) == -1
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_filter_autotune(None, 100)
+    assert ei.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BfError) as ei:
+        bf.bf_filter_tune_query(None, 0)
+    assert ei.value.status == bf.BF_EINVAL
+    L.bf_tune_check_target.restype = ctypes.c_int
+    L.bf_tune_check_target.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32]
+    assert L.bf_tune_check_target(None, b"x", 103, 152) == bf.BF_EINVAL
+    assert L.bf_tune_check_target(b"/nonexistent/t.json", None, 103, 152) == bf.BF_EINVAL
