@@ -164,3 +164,45 @@ def test_replay_drives_the_device_in_real_time(prec):
     assert r["jobs"] == 8 * 50 and 0 < r["p50_us"] <= r["p99_us"] <= r["max_us"] < 30_000, r
     assert len(errs) == 60 and max(errs) <= 1e-5, (len(errs), max(errs))
     print("replay, 60 TTIs:", {k: r[k] for k in ("p50_us", "p99_us", "max_us", "late_submits")})
+
+
+def test_watchdog_on_the_gpu_gives_up_late_launches_and_carries_on(plan):
+    """The watchdog on real launches, without a fault: with a 1 us limit every
+    launch (tens of microseconds on the device) is given up, its jobs report
+    BF_ETIMEOUT and count as timed out, and the slot is reused only after the
+    launch really completes -- so the R of a given-up job is still the right
+    result once the device is idle. A second server with the default limit on
+    the same plan then serves the same jobs normally, bit for bit."""
+    srv = bf.bf_serve_create(plan, n_slots=2, max_batch_jobs=1, hbm_budget_bytes=8 << 30, slot_timeout_us=1)
+    try:
+        cell = Cell(srv, 0, 36, 3000, 91)
+        torch.cuda.synchronize()
+        Rs = [cell.new_R(30) for _ in range(4)]
+        torch.cuda.synchronize()
+        ts = [bf.bf_submit(srv, cell.groups(30), bf.BF_BF16X3, cell.Sd, R) for R in Rs]
+        for t in ts:
+            with pytest.raises(bf.BfError) as ei:
+                bf.bf_wait(srv, t, 10_000_000)
+            assert ei.value.status == bf.BF_ETIMEOUT
+        st = bf.bf_serve_get_stats(srv)
+        assert st["timed_out"] == 4 and st["completed"] == 4 and st["slot_timeout_ns"] == 1000
+    finally:
+        bf.bf_serve_destroy(srv)  # waits until the given-up launches have completed
+    torch.cuda.synchronize()
+    got = [_R_np(R, 30) for R in Rs]
+    srv = bf.bf_serve_create(plan, n_slots=2, max_batch_jobs=1, hbm_budget_bytes=8 << 30)
+    try:
+        cell = Cell(srv, 0, 36, 3000, 91)  # the same precoders and S
+        torch.cuda.synchronize()
+        R2 = cell.new_R(30)
+        torch.cuda.synchronize()
+        bf.bf_wait(srv, bf.bf_submit(srv, cell.groups(30), bf.BF_BF16X3, cell.Sd, R2), 10_000_000)
+        want = _R_np(R2, 30)
+        assert bf.bf_serve_get_stats(srv)["timed_out"] == 0
+    finally:
+        bf.bf_serve_destroy(srv)
+    for g in got:
+        assert np.array_equal(g.view(np.uint64), want.view(np.uint64))
+    e = oracle.rel_frobenius([want.reshape(-1, 64, 60)],
+                             [np.concatenate(cell.reference(30)).reshape(-1, 64, 60)])
+    assert e < 1e-5
