@@ -129,7 +129,10 @@ def test_ragged_counts(filt, n_sig):
 
 def test_full_size_every_block(filt):
     """The bench workload (16 slots x 64 antennas x 14 symbols = 14,336 blocks)
-    in the bench's launch form, every block against the oracle."""
+    in the bench's launch form, every block against the oracle; the same batch
+    through the 12-warp building block (the autotuner's choice at this size)
+    gives the same bits, and through the three-pass one every block is checked
+    against the oracle too."""
     b = wl.config_filter_bench().rounded()
     y = run(filt, b.h, b.s)
     ref = oracle.circular_filter(b.h, b.s)
@@ -137,6 +140,16 @@ def test_full_size_every_block(filt):
     assert e <= TOL
     worst = assert_per_block(y, ref, "full size")
     print(f"filter full size: batch {e:.3e}, worst block {worst:.3e}")
+    try:
+        bf.bf_filter_set_variant(filt, 5)
+        y5 = run(filt, b.h, b.s, set_taps=False)
+        assert np.array_equal(y5.view(np.uint64), y.view(np.uint64))
+        bf.bf_filter_set_variant(filt, 4)
+        y4 = run(filt, b.h, b.s, set_taps=False)
+        worst4 = assert_per_block(y4, ref, "full size, three-pass")
+        print(f"filter full size, three-pass: batch {rel(y4, ref):.3e}, worst block {worst4:.3e}")
+    finally:
+        bf.bf_filter_set_variant(filt, 0)
 
 
 def test_in_place_host_and_determinism(filt):
