@@ -52,7 +52,10 @@ constexpr int SIMT_RPW = BF_SIMT_RPW;
 static_assert(SIMT_RPW == 8 || SIMT_RPW == 16, "rows per warp");
 constexpr int SIMT_CWARPS = N_ANT / SIMT_RPW;          // compute warps
 constexpr int SIMT_THREADS = (SIMT_CWARPS + 1) * 32;   // + one producer warp
-constexpr int SIMT_MIN_CTAS = SIMT_RPW == 8 ? 2 : 3;   // resident CTAs per SM the registers allow
+#ifndef BF_SIMT_MIN_CTAS
+#define BF_SIMT_MIN_CTAS (SIMT_RPW == 8 ? 2 : 3)
+#endif
+constexpr int SIMT_MIN_CTAS = BF_SIMT_MIN_CTAS;        // resident CTAs per SM the registers allow
 constexpr int SIMT_NS = BF_SIMT_NS;                    // S ring stages
 constexpr int SIMT_NW = 2;                             // W buffers
 constexpr int SIMT_S_STAGE = F_LIMIT * S_BYTES_PER_F;  // 17,280 B
