@@ -83,6 +83,9 @@ typedef struct {
     int64_t worst_latency_ns, worst_submit_ns, worst_queue_ns, worst_launch_ns, worst_device_ns;
     /* Over-deadline jobs by the largest of those four parts of their latency. */
     int64_t over_by_submit, over_by_queue, over_by_launch, over_by_device;
+    /* The four parts summed over every job that left the engine (divide by
+     * completed for the means). */
+    int64_t sum_submit_ns, sum_queue_ns, sum_launch_ns, sum_device_ns;
 } bf_serve_stats;
 
 /* Monotonic clock (CLOCK_MONOTONIC) in nanoseconds, the clock of arrival_ns. */

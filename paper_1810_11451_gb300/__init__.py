@@ -559,7 +559,8 @@ class bf_serve_stats(ctypes.Structure):
                 ("slot_timeout_ns", c_int64), ("worst_latency_ns", c_int64), ("worst_submit_ns", c_int64),
                 ("worst_queue_ns", c_int64), ("worst_launch_ns", c_int64), ("worst_device_ns", c_int64),
                 ("over_by_submit", c_int64), ("over_by_queue", c_int64), ("over_by_launch", c_int64),
-                ("over_by_device", c_int64)]
+                ("over_by_device", c_int64), ("sum_submit_ns", c_int64), ("sum_queue_ns", c_int64),
+                ("sum_launch_ns", c_int64), ("sum_device_ns", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

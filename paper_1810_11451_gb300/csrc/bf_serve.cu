@@ -91,6 +91,10 @@ static void account_done(bf_server_s *srv, JobRec &j) {
                              j.launched_ns && j.admit_ns ? j.launched_ns - j.admit_ns : 0,
                              j.launched_ns ? j.done_ns - j.launched_ns : 0};
     bf_serve_stats &st = srv->stats;
+    st.sum_submit_ns += part[0];
+    st.sum_queue_ns += part[1];
+    st.sum_launch_ns += part[2];
+    st.sum_device_ns += part[3];
     if (lat > st.deadline_ns) {
         st.over_deadline++;
         const int k = (int)(std::max_element(part, part + 4) - part);

@@ -11,6 +11,8 @@ Device-resident pools stand in for the radio: per cell a seeded S pool of
 precoders for every f, and a ring of R buffers. The schedule (with its
 precoder updates) is built beforehand and replayed by the library's native
 load generator (`bf_serve_replay`), so no interpreter sits in the timing loop.
+Every precoder update is scheduled before the earliest job of its epoch (the
+arrival jitter can bring a job ahead of the nominal update time).
 """
 from __future__ import annotations
 
@@ -76,21 +78,29 @@ class ServingSim:
     def run(self, jobs, warm_tti=20, tti_ns=500_000, sample_every=0, seed=0):
         """Submit `jobs` (workloads.ServingJob, sorted by arrival) in real time.
         Returns a dict of latency percentiles and throughput. A cell's
-        precoders for an epoch are set half a TTI before the epoch starts, into
-        the bank the previous epoch does not use, spaced 25 us apart across
-        cells (update-only items of the schedule). With sample_every = k > 0,
+        precoders for an epoch are set half a TTI before the epoch starts (or
+        20 us before the epoch's earliest job, if the jitter brings one
+        earlier), into the bank the previous epoch does not use, spaced 25 us
+        apart across cells (update-only items of the schedule). With sample_every = k > 0,
         one seeded random block of every k-th job is copied to the host as
         soon as the job completes (before its R buffer is reused) and returned
         under "samples" with the indices that locate its W and S."""
         srv = self.srv
         f_arrays = {f: (ctypes.c_int32 * N_RB_MAX)(*([f] * N_RB_MAX)) for f in range(1, 37)}
-        first = {}  # (cell, epoch) -> (first tti, f)
+        first = {}  # (cell, epoch) -> (first tti, f, earliest arrival in ns)
         for j in jobs:
             k = (j.cell, j.epoch)
-            if k not in first or j.tti < first[k][0]:
-                first[k] = (j.tti, j.f)
-        events = [(tti * tti_ns - tti_ns // 2 + cell * 25_000, 0, (cell, epoch, f))
-                  for (cell, epoch), (tti, f) in first.items()]
+            a = int(j.arrival_s * 1e9)
+            if k not in first:
+                first[k] = (j.tti, j.f, a)
+            else:
+                t0_, f0_, a0_ = first[k]
+                first[k] = (min(t0_, j.tti), f0_, min(a0_, a))
+        # an epoch's precoders are set half a TTI before the epoch (25 us apart
+        # across cells), and in any case 20 us before the epoch's earliest job:
+        # with the arrival jitter a job can come earlier than the nominal time
+        events = [(min(tti * tti_ns - tti_ns // 2 + cell * 25_000, a_min - 20_000), 0, (cell, epoch, f))
+                  for (cell, epoch), (tti, f, a_min) in first.items()]
         events += [(int(j.arrival_s * 1e9), 1, j) for j in jobs]
         events.sort(key=lambda e: (e[0], e[1]))
         items = (bf.bf_replay_item * len(events))()
@@ -178,6 +188,8 @@ class ServingSim:
                                     for k in ("latency", "submit", "queue", "launch", "device")},
                        "over_deadline_by_largest_part": {k: stats[f"over_by_{k}"]
                                                          for k in ("submit", "queue", "launch", "device")},
+                       "mean_us": {k: stats[f"sum_{k}_ns"] * 1e-3 / max(1, stats["completed"])
+                                   for k in ("submit", "queue", "launch", "device")},
                        "note": "counted by the server over every job, warm-up TTIs included"},
             **({"samples": samples} if sample_every else {}),
         }

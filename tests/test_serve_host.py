@@ -272,6 +272,9 @@ def test_deadline_accounting_and_worst_job(bf):
         # the late jobs waited in the queue behind the single slot longer than their own launch ran
         by = [st[k] for k in ("over_by_submit", "over_by_queue", "over_by_launch", "over_by_device")]
         assert sum(by) == st["over_deadline"] and st["over_by_queue"] >= 1
+        # the sums of the four parts add up to the sum of the latencies
+        total = sum(st[f"sum_{k}_ns"] for k in ("submit", "queue", "launch", "device"))
+        assert abs(total * 1e-3 - sum(lats)) < 4.0 and st["sum_device_ns"] >= 4 * 2_900_000
     finally:
         bf.bf_serve_destroy(srv)
     srv = bf.bf_serve_create(None, n_slots=2, hbm_budget_bytes=1 << 30, fake_device_us=100)
