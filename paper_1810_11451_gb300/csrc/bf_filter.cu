@@ -356,13 +356,15 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 //    output (j, q) goes back to the place it came from, E[j + 64 q], so each
 //    of the two butterflies of a lane touches only its own column;
 //  - inverse pass A' (radix 64, Ns = 32): butterfly j = l needs inverse
-//    values (m, j), m < 64, which is row j of E; it twists them by
-//    e^{+2 pi i j m / N} and stores y[j + 32 q], coalesced.
+//    values (m, j), m < 64, which is row j of E, twisted by
+//    e^{+2 pi i j m / N}; that twist is applied by pass B' before its store,
+//    with the twiddles it still holds from pass B (the same values), and
+//    pass A' stores y[j + 32 q], coalesced.
 // Both transforms run the forward DFT code: the inverse DFT of z is the
 // conjugate of the forward DFT of conj(z). So the product writes
 // conj(X H / N) (conjugation folded into the multiply), E holds conjugated
-// inverse values, pass A' twists them by the forward twiddles, and y is the
-// conjugate of its last DFT. The 64- and 32-point DFTs run in registers as
+// inverse values twisted by the forward twiddles, and y is the conjugate of
+// its last DFT. The 64- and 32-point DFTs run in registers as
 // 8 x 8 and 8 x 4 splits with constant twiddles, each once in the code (two
 // loops of two rounds), so the loop body stays small. The pass twiddles come
 // from a 64 x 32 table e^{-2 pi i a b / N} (row stride 33); E has one pad per
@@ -533,10 +535,17 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const int j = l + 32 * h;
-                float2 u[32];
+                // e^{-2 pi i j m / N}, m < 32: pass B's twiddles, and also the
+                // ones pass A' needs on this column's inverse outputs (value
+                // (j, q) goes to butterfly q of pass A' as its input j, twisted
+                // by e^{-2 pi i j q / N} in the conjugated domain), applied here
+                // before the store so pass A' reads its inputs ready
+                float2 tw[32], u[32];
+#pragma unroll
+                for (int m = 1; m < 32; ++m) tw[m] = TB[j * TB_ROW + m];
                 u[0] = E[padf(j)];
 #pragma unroll
-                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
+                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], tw[m]);
 #pragma unroll 1
                 for (int sub = 0;; ++sub) {
                     dft32(u);
@@ -548,14 +557,14 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
 #pragma unroll
                     for (int m = 0; m < 32; ++m) u[m] = t[m];
                 }
+                E[padf(j)] = u[pos32(0)];
 #pragma unroll
-                for (int q2 = 0; q2 < 32; ++q2) E[padf(j + 64 * q2)] = u[pos32(q2)];
+                for (int q2 = 1; q2 < 32; ++q2) E[padf(j + 64 * q2)] = cmul(u[pos32(q2)], tw[q2]);
             }
             __syncwarp();
-            // inverse pass A' input: row l of E (conjugated values), forward twiddles
-            v[0] = E[padf(64 * l)];
+            // inverse pass A' input: row l of E (conjugated, already twisted)
 #pragma unroll
-            for (int m = 1; m < 64; ++m) v[m] = cmul(E[padf(64 * l + m)], TB[m * TB_ROW + l]);
+            for (int m = 0; m < 64; ++m) v[m] = E[padf(64 * l + m)];
             __syncwarp();  // E is free: copy the next block in while this one finishes
             if (q + stride < n_sig) stage_block(E, s + (q + stride) * N, l);
         }
