@@ -621,7 +621,7 @@ struct bf_filter_s {
     size_t slot_cap = 0;  // blocks per slot
     int slot_next = 0;    // next slot (the ring continues across calls)
     bool s_indep = false; // bf_filter_set_s_independent
-    int variant = 0;      // bf_filter_set_variant
+    int variant = 2;      // bf_filter_set_variant (default: 8 warps per CTA)
     double tuned_us[6] = {};  // bf_filter_autotune: microseconds per launch of each variant (0: not timed)
     int64_t tuned_n_sig = 0;
     std::string device_name;

@@ -149,7 +149,7 @@ def test_full_size_every_block(filt):
         worst4 = assert_per_block(y4, ref, "full size, three-pass")
         print(f"filter full size, three-pass: batch {rel(y4, ref):.3e}, worst block {worst4:.3e}")
     finally:
-        bf.bf_filter_set_variant(filt, 0)
+        bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
 
 
 def test_in_place_host_and_determinism(filt):
@@ -183,6 +183,7 @@ def test_errors(filt):
         assert ei.value.status == bf.BF_EINVAL
     f2 = bf.bf_filter_create(N)
     try:
+        assert bf.bf_filter_get_variant(f2) == bf.FILTER_DEFAULT_VARIANT
         s = dev_c64(np.ones((2, N))).view(-1)  # flat float32 view of two blocks
         with pytest.raises(bf.BfError) as ei:
             bf.bf_filter_apply(f2, s, 2, s)
@@ -274,6 +275,7 @@ def test_variants_bit_identical_and_accurate(filt):
             outs[v] = host_c64(y_d).reshape(b.n_sig, N)
         for v in (1, 2, 3, 5):
             assert np.array_equal(outs[v].view(np.uint64), outs[0].view(np.uint64)), f"variant {v}"
+        assert bf.FILTER_DEFAULT_VARIANT in (0, 1, 2, 3, 5)
         ref = oracle.circular_filter(b.h, b.s)
         for v in (0, 4):
             assert_per_block(outs[v], ref, f"variant {v}")
@@ -281,7 +283,7 @@ def test_variants_bit_identical_and_accurate(filt):
             bf.bf_filter_set_variant(filt, 6)
         assert ei.value.status == bf.BF_EINVAL
     finally:
-        bf.bf_filter_set_variant(filt, 0)
+        bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
 
 
 def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
@@ -299,7 +301,7 @@ def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
         assert v in (0, 1, 2, 3, 5)
         times = {k: bf.bf_filter_tune_query(filt, k) for k in range(6)}
         assert all(t > 0 and n == 4096 for t, n in times.values()), times
-        assert times[v][0] <= times[0][0]
+        assert times[v][0] <= times[bf.FILTER_DEFAULT_VARIANT][0]  # no slower than the default
         y1 = torch.full_like(s_d, float("nan"))
         bf.bf_filter_apply(filt, s_d, b.n_sig, y1)
         torch.cuda.synchronize()
@@ -330,4 +332,4 @@ def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
         finally:
             bf.bf_filter_destroy(other)
     finally:
-        bf.bf_filter_set_variant(filt, 0)
+        bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
