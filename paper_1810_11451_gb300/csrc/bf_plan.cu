@@ -554,6 +554,14 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
     int cur = 0;
     int64_t k = 0;
     int blk = 0;
+    // precoder-run flags within each CTA's range, counting tiles with f > 0
+    // only, set as the tiles are made: the first tile of a run of one precoder
+    // and the last one (closed when another precoder starts or the range ends)
+    int prev = -1, last_idx = -1;
+    auto close_range = [&] {
+        if (last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
+        prev = last_idx = -1;
+    };
     for (int g = 0; g < n_groups; ++g) {
         const bf_group &gr = groups[g];
         const int f = f_slot[gr.prec_id];
@@ -561,41 +569,42 @@ void build_worklist(const int *f_slot, const TuneTable &tune, const bf_group *gr
         const int tile_blocks = tune.tile_blocks_for(prec, f);
         int pos = 0;
         while (pos < gr.n_blocks) {
-            while (cur + 1 < n_cta && bnd[cur + 1] <= k + pos) cta_begin[++cur] = n_tiles;  // a range starts here
-            const int stop = cur + 1 < n_cta ? (int)std::min<int64_t>(gr.n_blocks, bnd[cur + 1] - k) : gr.n_blocks;
-            for (int b = pos; b < stop; b += tile_blocks) {
-                Tile &t = tiles[n_tiles++];
-                t.s_off = gr.s_off + (int64_t)b * sb;
-                t.r_off = gr.r_off + (int64_t)b * r_block_stride;
-                t.prec = gr.prec_id;
-                t.sblk = blk + b;
-                t.f = (int16_t)f;
-                t.nblk = (int16_t)std::min(tile_blocks, stop - b);
-                t.flags = 0;
+            while (cur + 1 < n_cta && bnd[cur + 1] <= k + pos) {  // a range starts here
+                close_range();
+                cta_begin[++cur] = n_tiles;
             }
+            const int stop = cur + 1 < n_cta ? (int)std::min<int64_t>(gr.n_blocks, bnd[cur + 1] - k) : gr.n_blocks;
+            const int32_t first_flag = (f > 0 && stop > pos && gr.prec_id != prev) ? TF_FIRST_OF_W : 0;
+            if (f > 0 && stop > pos) {
+                if (first_flag && last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
+                prev = gr.prec_id;
+            }
+            int64_t s_off = gr.s_off + (int64_t)pos * sb, r_off = gr.r_off + (int64_t)pos * r_block_stride;
+            const int64_t s_step = (int64_t)tile_blocks * sb, r_step = (int64_t)tile_blocks * r_block_stride;
+            Tile *t = tiles + n_tiles;
+            for (int b = pos; b < stop; b += tile_blocks, ++t, s_off += s_step, r_off += r_step) {
+                t->s_off = s_off;
+                t->r_off = r_off;
+                t->prec = gr.prec_id;
+                t->sblk = blk + b;
+                t->f = (int16_t)f;
+                t->nblk = (int16_t)std::min(tile_blocks, stop - b);
+                t->flags = 0;
+            }
+            const int made = (int)(t - (tiles + n_tiles));
+            if (f > 0 && made > 0) {
+                tiles[n_tiles].flags |= first_flag;
+                last_idx = n_tiles + made - 1;
+            }
+            n_tiles += made;
             pos = stop;
         }
         k += gr.n_blocks;
         blk += gr.n_blocks;
     }
+    close_range();
     wl.n_tiles = n_tiles;
     cta_begin[n_cta] = n_tiles;
-    // precoder-run flags within each CTA's range (tiles with f > 0 only)
-    for (int c = 0; c + 1 < (int)wl.cta_begin.size(); ++c) {
-        int prev = -1;
-        int last_idx = -1;
-        for (int t = wl.cta_begin[c]; t < wl.cta_begin[c + 1]; ++t) {
-            Tile &tl = tiles[t];
-            if (tl.f == 0) continue;
-            if (tl.prec != prev) {
-                tl.flags |= TF_FIRST_OF_W;
-                if (last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
-            }
-            prev = tl.prec;
-            last_idx = t;
-        }
-        if (last_idx >= 0) tiles[last_idx].flags |= TF_LAST_OF_W;
-    }
 }
 
 extern "C" int32_t bf_schedule(const int32_t *f_of_slot, int32_t n_slots, const bf_group *groups, int32_t n_groups,
