@@ -816,7 +816,11 @@ def main():
                            "peak_tflops": fma["tflops"], "frac": flops / (p_ms * 1e-3) / 1e12 / fma["tflops"],
                            "peak": fma}},
         "fp32_3m": {"value": world * flops / (p3_ms * 1e-3) / 1e9 if p3_ms == p3_ms else None, "unit": UNIT,
-                    "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add"},
+                    "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add",
+                    "frac_of_fma_peak": None if fma is None or p3_ms != p3_ms else
+                    flops / (p3_ms * 1e-3) / 1e12 / fma["tflops"],
+                    "frac_note": "conventional flops (8 per complex multiply-add) over the measured FMA rate; "
+                                 "the form issues 6 of them as FMAs"},
         "tf32x3": {"value": world * flops / (t32_ms * 1e-3) / 1e9 if t32_ms == t32_ms else None, "unit": UNIT,
                    "kernel_ms": t32_ms, "hbm_gbs": alg_bytes / (t32_ms * 1e-3) / 1e9 if t32_ms == t32_ms else None,
                    "form": "split-tf32 (hi*hi + hi*lo + lo*hi) tcgen05 kind::tf32, FP32 accumulate"},
