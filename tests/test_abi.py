@@ -227,3 +227,22 @@ def test_new_entry_points_reject_bad_arguments_before_cuda(bf):
     L.bf_tune_check_target.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32]
     assert L.bf_tune_check_target(None, b"x", 103, 152) == bf.BF_EINVAL
     assert L.bf_tune_check_target(b"/nonexistent/t.json", None, 103, 152) == bf.BF_EINVAL
+
+
+@pytest.mark.parametrize("max_cta", [1, 2, 3, 5])
+def test_scheduler_flags_with_shared_slots_and_empty_flows(bf, max_cta):
+    """Consecutive groups on the same precoder slot form one run (no new first
+    flag), f = 0 tiles carry no flags and do not break a run, and ranges start
+    new runs: the flags equal their definition, worked out in Python."""
+    f_of_slot = [36, 0, 8]
+    groups = [(0, 5, 0, 0), (0, 3, 0, 0), (1, 2, 0, 0), (0, 2, 0, 0), (2, 4, 0, 0), (2, 1, 0, 0)]
+    tiles, begin = schedule(bf, f_of_slot, groups, bf.BF_BF16X3, 0, max_cta)
+    for t in tiles:
+        if t.f == 0:
+            assert t.flags == 0
+    for c in range(len(begin) - 1):
+        run = [t for t in tiles[begin[c]:begin[c + 1]] if t.f > 0]
+        for i, t in enumerate(run):
+            first = i == 0 or run[i - 1].prec_id != t.prec_id
+            last = i == len(run) - 1 or run[i + 1].prec_id != t.prec_id
+            assert bool(t.flags & 1) == first and bool(t.flags & 2) == last, (c, i, t.prec_id, t.flags)
