@@ -730,13 +730,18 @@ def main():
     fma = None
     if not args.no_plain:
         with ClockSampler(local) as fclk:
-            fma_tf, fma_ms = bf.bf_measure_fp32_peak(20000, 5, False, stream)
-            fma2_tf, _ = bf.bf_measure_fp32_peak(10000, 5, True, stream)
-        # the peak is the faster of scalar and packed FP32x2 FMAs
+            fma_tf, fma_ms = bf.bf_measure_fp32_peak(20000, 5, 0, stream)
+            fma2_tf, _ = bf.bf_measure_fp32_peak(10000, 5, 1, stream)
+            outer_tf, _ = bf.bf_measure_fp32_peak(20000, 5, 2, stream)
+        # the peak is the faster of scalar and packed FP32x2 FMAs; the
+        # outer-product operand pattern (two new register pairs per FMA, as in
+        # any product loop) is reported beside it as the ceiling of such a loop
         fma = {"tflops": max(fma_tf, fma2_tf), "scalar_tflops": fma_tf, "packed_tflops": fma2_tf,
+               "outer_product_tflops": outer_tf,
                "ms_per_launch": fma_ms, "clocks": fclk.summary(),
                "how": "bf_measure_fp32_peak: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
-                      "scalar and packed FP32x2, best of 5 launches each (CUDA events)"}
+                      "scalar and packed FP32x2 (one register operand per FMA), and packed FP32x2 over a 4 x 4 "
+                      "register-blocked outer product (mode 2); best of 5 launches each (CUDA events)"}
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -814,6 +819,7 @@ def main():
                        "roofline": None if fma is None or p_ms != p_ms else {
                            "bound": "fma", "achieved_tflops": flops / (p_ms * 1e-3) / 1e12,
                            "peak_tflops": fma["tflops"], "frac": flops / (p_ms * 1e-3) / 1e12 / fma["tflops"],
+                           "frac_of_outer_product_rate": flops / (p_ms * 1e-3) / 1e12 / fma["outer_product_tflops"],
                            "peak": fma}},
         "fp32_3m": {"value": world * flops / (p3_ms * 1e-3) / 1e9 if p3_ms == p3_ms else None, "unit": UNIT,
                     "kernel_ms": p3_ms, "form": "FP32 CUDA cores, three real products per complex multiply-add",

@@ -442,13 +442,19 @@ bf_status bf_errnorm_noalloc(const void *R_dev, const void *Rref_dev, int64_t n_
  * the roofline denominator of the plain FP32 form: at f = 36 that form does
  * 22.4 flop per algorithmic byte, above the CUDA-core ridge, so its bound is
  * FMA issue (Sec. III: the paper's improved kernel is built on FMA). One
- * kernel of 4 CTAs of 256 threads per SM runs 8 independent chains of
- * 4 * iters FMAs per thread, scalar (packed = 0) or packed FP32x2 FMAs
- * (packed = 1, 4 flop each); after one warm-up launch, the best of `reps`
- * launches timed with CUDA events on `stream` gives *tflops_host (2 flop per
- * FMA) and *ms_host (may be NULL). iters in [1, 2^24], reps in [1, 1000],
- * else BF_EINVAL. Synchronises `stream`. */
-bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, int32_t packed, double *tflops_host, double *ms_host,
+ * kernel of 4 CTAs of 256 threads per SM, by `mode`:
+ *  0: 8 independent chains of 4 * iters scalar FMAs per thread;
+ *  1: the same with packed FP32x2 FMAs (4 flop each);
+ *  2: packed FP32x2 FMAs in the operand pattern of a register-blocked outer
+ *     product, 16 accumulator pairs over 4 x 4 operand pairs, 16 * iters
+ *     FMAs per thread. Modes 0 and 1 read one register operand per FMA (the
+ *     others are kernel arguments); mode 2 reads three, two of them new, as
+ *     every product loop must, so its rate is the ceiling of such a loop.
+ * After one warm-up launch, the best of `reps` launches timed with CUDA
+ * events on `stream` gives *tflops_host (2 flop per FMA) and *ms_host (may
+ * be NULL). iters in [1, 2^24], reps in [1, 1000], mode 0..2, else
+ * BF_EINVAL. Synchronises `stream`. */
+bf_status bf_measure_fp32_peak(int32_t iters, int32_t reps, int32_t mode, double *tflops_host, double *ms_host,
                                void *stream);
 
 /* Number of product kernels (or graph replays) this plan has launched so far

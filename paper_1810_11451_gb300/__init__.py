@@ -521,13 +521,14 @@ def bf_errnorm_noalloc(R_dev, Rref_dev, n_blocks: int, stream=None) -> Tuple[flo
     return float(tot[0]), float(tot[1])
 
 
-def bf_measure_fp32_peak(iters: int = 20000, reps: int = 5, packed: bool = False, stream=None) -> Tuple[float, float]:
-    """(TFLOP/s, ms per launch) of the CUDA cores' FP32 FMA probe (scalar or packed FP32x2)."""
+def bf_measure_fp32_peak(iters: int = 20000, reps: int = 5, mode: int = 0, stream=None) -> Tuple[float, float]:
+    """(TFLOP/s, ms per launch) of the CUDA cores' FP32 FMA probe: mode 0 scalar, 1 packed FP32x2,
+    2 packed FP32x2 in a register-blocked outer-product operand pattern."""
     L = lib()
     L.bf_measure_fp32_peak.restype = c_int
     L.bf_measure_fp32_peak.argtypes = [c_int32, c_int32, c_int32, POINTER(c_double), POINTER(c_double), c_void_p]
     t, ms = c_double(), c_double()
-    st = L.bf_measure_fp32_peak(int(iters), int(reps), int(bool(packed)), ctypes.byref(t), ctypes.byref(ms),
+    st = L.bf_measure_fp32_peak(int(iters), int(reps), int(mode), ctypes.byref(t), ctypes.byref(ms),
                                 _stream(stream))
     if st != BF_OK:
         raise BfError(st, bf_last_error(None))

@@ -210,8 +210,8 @@ def test_new_entry_points_reject_bad_arguments_before_cuda(bf):
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_void_p]
     t, ms = ctypes.c_double(), ctypes.c_double()
-    for iters, reps, packed in [(0, 5, 0), (1 << 25, 5, 0), (10, 0, 0), (10, 1001, 0), (10, 5, 2)]:
-        assert L.bf_measure_fp32_peak(iters, reps, packed, ctypes.byref(t), ctypes.byref(ms), None) == bf.BF_EINVAL
+    for iters, reps, mode in [(0, 5, 0), (1 << 25, 5, 0), (10, 0, 0), (10, 1001, 0), (10, 5, 3), (10, 5, -1)]:
+        assert L.bf_measure_fp32_peak(iters, reps, mode, ctypes.byref(t), ctypes.byref(ms), None) == bf.BF_EINVAL
     assert L.bf_measure_fp32_peak(10, 5, 0, None, None, None) == bf.BF_EINVAL
     with pytest.raises(bf.BfError) as ei:
         bf.bf_filter_set_variant(None, 0)
