@@ -516,11 +516,11 @@ def filter_leg(torch, bf, b, sample, stream, steps=100, variant=None):
     h = to_device_c64(b.h, torch)
     bf.bf_filter_set_taps(f, h, len(b.h), stream)
     bf.bf_filter_set_s_independent(f)  # S is filled once, by a copy; the filter never writes it
-    # the building block for this size on this GPU (bit-identical candidates),
+    # the building block for this size on this GPU (the fastest variant),
     # unless a variant is named
     if variant is None:
         chosen = bf.bf_filter_autotune(f, b.n_sig, stream)
-        variants = {bf.FILTER_VARIANTS[v]: bf.bf_filter_tune_query(f, v)[0] for v in range(6)}
+        variants = {bf.FILTER_VARIANTS[v]: bf.bf_filter_tune_query(f, v)[0] for v in range(len(bf.FILTER_VARIANTS))}
     else:
         bf.bf_filter_set_variant(f, variant)
         chosen, variants = variant, None

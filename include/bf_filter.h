@@ -94,12 +94,18 @@ bf_status bf_filter_set_s_independent(bf_filter filter, int32_t independent);
  *       block, 4 blocks per CTA, the next block prefetched into shared memory
  *   5 : the two-pass kernel with 12 warps per CTA, the spectrum read through
  *       L1 instead of shared memory
- * Variants 0 to 3 and 5 give bit-identical results; variant 4 rounds
- * differently (another factorisation) within the same accuracy. The spectrum
- * of the taps is always computed the same way, whatever the variant. */
+ *   6 : two passes per transform (2048 = 32 x 64), two warps per block,
+ *       32 values a lane, 8 blocks per CTA; the radix-64 pass is split over
+ *       lane pairs that exchange half their values by shuffles. A block
+ *       finishes in about half the time of the one-warp kernels, which pays
+ *       on small batches (one round of blocks or less)
+ * Variants 0 to 3 and 5 give bit-identical results; variants 4 and 6 round
+ * differently (other factorisations) within the same FP32 accuracy. The
+ * spectrum of the taps is always computed the same way, whatever the
+ * variant. */
 
 /* Select the variant used by bf_filter_apply and bf_filter_apply_host
- * (BF_EINVAL outside [0, 6)). */
+ * (BF_EINVAL outside [0, 7)). */
 bf_status bf_filter_set_variant(bf_filter filter, int32_t variant);
 
 /* The variant in use (-1 for a NULL filter). */
@@ -107,8 +113,12 @@ int32_t bf_filter_get_variant(bf_filter filter);
 
 /* Time every variant on this GPU on n_sig synthetic blocks (1 <= n_sig <=
  * 2^20; scratch of 2 x n_sig x 16 KB is allocated and freed here; the best
- * of 3 rounds of 10 back-to-back launches) and select the fastest of the
- * bit-identical variants 0 to 3 and 5 (so tuning never changes a result bit).
+ * of 3 rounds of 10 back-to-back launches, made as bf_filter_apply would
+ * make them: with s independent if bf_filter_set_s_independent declared it,
+ * which lets each launch's prologue overlap the previous launch and favours
+ * other variants on small batches) and select the fastest. Every
+ * variant computes in FP32 to the same accuracy, but variants 4 and 6 round
+ * differently from the others, so tuning can change low-order result bits.
  * Runs on `stream` and synchronises it. BF_ENOTFOUND if no taps are set. */
 bf_status bf_filter_autotune(bf_filter filter, int64_t n_sig, void *stream);
 

@@ -5,6 +5,8 @@
 //  - bf_filter_warp_kernel (the default; see its own comment further down):
 //    one warp per block of samples, two Stockham passes per transform
 //    (2048 = 64 x 32), the block crossing shared memory once per transform;
+//  - bf_filter_pair_kernel (see its comment): two warps per block, two
+//    passes per transform (2048 = 32 x 64);
 //  - bf_filter_kernel, described here: three passes per transform.
 //
 // Three-pass form. A team of 128 threads filters one block of 2048 samples;
@@ -601,6 +603,169 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// Pair form: two warps (64 lanes) per block, 32 values per lane, 2048 =
+// 32 x 64. Half the registers of the one-warp form, so an SM runs 16 warps
+// (four per sub-partition) instead of 8, and each block crosses shared
+// memory once per transform as before:
+//  - forward pass 1 (radix 32, Ns = 1): lane L = 32 w + l (w: warp of the
+//    pair) is butterfly L, x[L + 64 m], m < 32, and writes E[32 L + q];
+//  - forward pass 2 (radix 64, Ns = 32), split over lane pairs: butterfly
+//    j = 16 w + (l & 15) belongs to lanes l < 16 (r = 0) and l + 16 (r = 1)
+//    of warp w. Lane r reads the inputs m = 16 r + i and m + 32 (i < 16),
+//    twisted by e^{-2 pi i j m / N} (the 64 x 32 table read transposed), and
+//    takes the first radix-2 step of the 64-point DFT (decimation in
+//    frequency): b = a_m + a_{m+32}, c = (a_m - a_{m+32}) e^{-2 pi i m / 64}.
+//    One exchange of 16 values with the partner (shuffle, lane xor 16) gives
+//    lane r = 0 all 32 b and lane r = 1 all 32 c, whose 32-point DFTs are
+//    the even and odd outputs X[j + 32 k], k = 2 s + r;
+//  - the product with H / N (conjugated, as in the one-warp form) in
+//    registers; lanes r = 0 and 1 then hold the even and odd inputs of the
+//    inverse's radix-64 butterfly j, so the inverse pass 1 starts in
+//    registers with a 32-point DFT and ends with one radix-2 step
+//    (decimation in time) after a second exchange, and writes E[64 j + q];
+//  - inverse pass 2 (radix 32, Ns = 64): lane L reads E[L + 64 m] twisted by
+//    the table and stores y[L + 64 q], coalesced.
+// The exchange buffer has one pad per 32 values and one more per 512, which
+// keeps every access of a half-warp free of bank conflicts in all four
+// patterns. The two warps of a pair meet at a named barrier between passes;
+// the next block is copied into E with cp.async while the last pass runs.
+constexpr int PBUF = 2114;  // padp(N - 1) + 1
+__host__ __device__ constexpr int padp(int e) { return e + (e >> 5) + (e >> 9); }
+static_assert(padp(N - 1) + 1 == PBUF, "pair exchange buffer");
+__host__ __device__ constexpr int psmem_bytes(int pairs) { return (TB_SIZE + N + pairs * PBUF) * 8; }
+static_assert(psmem_bytes(8) <= 232448, "8 pairs per CTA exceed the shared memory of one SM");
+
+// the two warps of pair `id` (named barrier id + 1; barrier 0 is __syncthreads)
+__device__ __forceinline__ void pair_sync(int id) {
+    asm volatile("bar.sync %0, 64;" ::"r"(id + 1) : "memory");
+}
+
+// The pair's copy of one block (16 KB) into E, unpadded: 16 asynchronous
+// 16-byte copies per lane (L < 64), one commit group.
+__device__ __forceinline__ void stage_block_pair(float2 *dst, const float2 *src, int L) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int off = (L + 64 * i) * 16;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + off), "l"(g + off) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// y = IFFT(Hs * FFT(s)), Hs = FFT(h) / N; launch ordering as bf_filter_kernel.
+template <int PAIRS>
+__global__ void __launch_bounds__(64 * PAIRS, 1)
+    bf_filter_pair_kernel(const float2 *s, float2 *y, long long n_sig, const float2 *__restrict__ tb_g,
+                          const float2 *__restrict__ H_g, int s_indep) {
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *TB = sm;
+    float2 *Hs = sm + TB_SIZE;
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int pair = warp >> 1, wp = warp & 1;
+    const int L = 32 * wp + l;              // passes 1 and 2': butterfly L
+    const int r = l >> 4;                   // passes 2 and 1': which half of butterfly j
+    const int j = 16 * wp + (l & 15);       // passes 2 and 1': butterfly j
+    float2 *E = sm + TB_SIZE + N + pair * PBUF;
+    for (int i = threadIdx.x; i < N + TB_SIZE; i += 64 * PAIRS) {
+        if (i < TB_SIZE) {
+            TB[i] = tb_g[i];
+        } else {
+            const float2 h = H_g[i - TB_SIZE];
+            Hs[i - TB_SIZE] = make_float2(h.x * (1.f / N), h.y * (1.f / N));
+        }
+    }
+    __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    bool dep_done = false;
+    if (!s_indep) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        dep_done = true;
+    }
+    // constant parts of the padded indices (see padp)
+    const int e1 = 33 * L + (L >> 4);           // pass 1 writes E[e1 + q]
+    const int e2 = j + 529 * r;                 // pass 2 reads E[e2 + 33 i] and E[e2 + 1058 + 33 i]
+    const int t2 = 528 * r + j;                 // and twiddles TB[t2 + 33 i], TB[t2 + 1056 + 33 i]
+    const int e3 = 66 * j + (j >> 3) + 16 * r;  // pass 1' writes E[e3 + i] and E[e3 + 33 + i]
+    const int e4 = L + wp;                      // pass 2' reads E[e4 + 66 m + (m >> 3)]
+    const long long stride = (long long)gridDim.x * PAIRS;
+    long long q = (long long)blockIdx.x * PAIRS + pair;
+    if (q < n_sig) stage_block_pair(E, s + q * N, L);
+    for (; q < n_sig; q += stride) {
+        float2 v[32];
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        pair_sync(pair);
+#pragma unroll
+        for (int m = 0; m < 32; ++m) v[m] = E[L + 64 * m];
+        pair_sync(pair);  // every lane has its inputs before E is overwritten
+        // forward pass 1
+        dft32(v);
+#pragma unroll
+        for (int q2 = 0; q2 < 32; ++q2) E[e1 + q2] = v[pos32(q2)];
+        pair_sync(pair);
+        // forward pass 2: twist, first radix-2 step, exchange, 32-point DFT
+        {
+            float2 bv[16], cv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float2 a0 = cmul(E[e2 + 33 * i], TB[t2 + 33 * i]);
+                const float2 a1 = cmul(E[e2 + 1058 + 33 * i], TB[t2 + 1056 + 33 * i]);
+                bv[i] = cadd(a0, a1);
+                const float2 c = twc(csub(a0, a1), i);      // e^{-2 pi i i / 64}
+                cv[i] = r ? cmul_i<-1>(c) : c;              // and e^{-2 pi i 16 / 64} = -i for r = 1
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float2 snd = r ? bv[i] : cv[i];
+                const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, snd.x, 16),
+                                               __shfl_xor_sync(0xffffffffu, snd.y, 16));
+                v[i] = r ? rcv : bv[i];
+                v[16 + i] = r ? cv[i] : rcv;
+            }
+        }
+        dft32(v);  // X[j + 32 (2 s + r)] at v[pos32(s)]
+        // product, conjugated: the inverse runs the forward DFT code
+        float2 u[32];
+#pragma unroll
+        for (int s2 = 0; s2 < 32; ++s2) u[s2] = cmul_conj(v[pos32(s2)], Hs[j + 32 * r + 64 * s2]);
+        // inverse pass 1: 32-point DFT of the even (r = 0) or odd (r = 1)
+        // inputs, exchange, last radix-2 step
+        dft32(u);  // G[k] at u[pos32(k)]
+        pair_sync(pair);  // the partner warp has finished reading E in pass 2
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float2 g0 = u[pos32(i)], g1 = u[pos32(16 + i)];
+            const float2 snd = r ? g0 : g1;
+            const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, snd.x, 16),
+                                           __shfl_xor_sync(0xffffffffu, snd.y, 16));
+            const float2 P = r ? rcv : g0;
+            float2 T = twc(r ? g1 : rcv, i);
+            T = r ? cmul_i<-1>(T) : T;
+            E[e3 + i] = cadd(P, T);
+            E[e3 + 33 + i] = csub(P, T);
+        }
+        pair_sync(pair);
+        // inverse pass 2: twist by the table, 32-point DFT, conjugate, store
+        v[0] = E[e4];
+#pragma unroll
+        for (int m = 1; m < 32; ++m) v[m] = cmul(E[e4 + 66 * m + (m >> 3)], TB[L * TB_ROW + m]);
+        pair_sync(pair);  // E is free: copy the next block in while this one finishes
+        if (q + stride < n_sig) stage_block_pair(E, s + (q + stride) * N, L);
+        dft32(v);
+        if (!dep_done) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            dep_done = true;
+        }
+        float2 *yq = y + q * N;
+#pragma unroll
+        for (int q2 = 0; q2 < 32; ++q2) {
+            const float2 rr = v[pos32(q2)];
+            yq[L + 64 * q2] = make_float2(rr.x, conj_im(rr.y));
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 }  // namespace bff
 
 using namespace bff;
@@ -622,7 +787,7 @@ struct bf_filter_s {
     int slot_next = 0;    // next slot (the ring continues across calls)
     bool s_indep = false; // bf_filter_set_s_independent
     int variant = 2;      // bf_filter_set_variant (default: 8 warps per CTA)
-    double tuned_us[6] = {};  // bf_filter_autotune: microseconds per launch of each variant (0: not timed)
+    double tuned_us[7] = {};  // bf_filter_autotune: microseconds per launch of each variant (0: not timed)
     int64_t tuned_n_sig = 0;
     std::string device_name;
     int cc = 0;
@@ -668,9 +833,11 @@ __global__ void bf_scale_spectrum_kernel(const float2 *H, float2 *Hn) {
 
 // The building blocks a filter can run (bf_filter_set_variant): the two-pass
 // kernel with 11, 10, 8 or 6 warps per CTA, or 12 with the spectrum read
-// through L1 (bit-identical results), and the three-pass kernel with four
-// 128-thread teams per CTA.
-constexpr int N_VARIANTS = 6;
+// through L1 (bit-identical results), the three-pass kernel with four
+// 128-thread teams per CTA, and the two-pass pair kernel with eight pairs of
+// warps per CTA (variant 6).
+constexpr int N_VARIANTS = 7;
+static_assert(N_VARIANTS == sizeof(bf_filter_s::tuned_us) / sizeof(double), "one tuned time per variant");
 
 template <bool FILTER, int WARPS, bool HG = false>
 static cudaError_t launch_warp(const float2 *s, float2 *y, long long n_sig, const bf_filter f, cudaStream_t st,
@@ -690,6 +857,30 @@ static cudaError_t launch_warp(const float2 *s, float2 *y, long long n_sig, cons
                               (const float2 *)(FILTER ? f->H : nullptr), s_indep ? 1 : 0, (const float2 *)f->Hn);
 }
 
+template <int PAIRS>
+static cudaError_t launch_pair(const float2 *s, float2 *y, long long n_sig, const bf_filter f, cudaStream_t st,
+                               bool s_indep) {
+    const long long want = (n_sig + PAIRS - 1) / PAIRS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(want, (long long)f->sm_count));
+    cfg.blockDim = dim3(64 * PAIRS);
+    cfg.dynamicSmemBytes = psmem_bytes(PAIRS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bf_filter_pair_kernel<PAIRS>, s, y, n_sig, (const float2 *)f->tb,
+                              (const float2 *)f->H, s_indep ? 1 : 0);
+}
+
+template <int PAIRS>
+static cudaError_t configure_pair() {
+    return cudaFuncSetAttribute(bf_filter_pair_kernel<PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                psmem_bytes(PAIRS));
+}
+
 template <bool FILTER, int WARPS, bool HG = false>
 static cudaError_t configure_warp() {
     return cudaFuncSetAttribute(bf_filter_warp_kernel<FILTER, WARPS, HG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -707,6 +898,7 @@ static cudaError_t launch_filter(bool filter, const float2 *s, float2 *y, long l
         case 2: return launch_warp<true, 8>(s, y, n_sig, f, st, s_indep);
         case 3: return launch_warp<true, 6>(s, y, n_sig, f, st, s_indep);
         case 5: return launch_warp<true, 12, true>(s, y, n_sig, f, st, s_indep);
+        case 6: return launch_pair<8>(s, y, n_sig, f, st, s_indep);
         case 4: break;
         default: return launch_warp<true, 11>(s, y, n_sig, f, st, s_indep);
     }
@@ -766,6 +958,7 @@ extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
               configure_warp<false, 11>() == cudaSuccess && configure_warp<true, 11>() == cudaSuccess &&
               configure_warp<true, 10>() == cudaSuccess && configure_warp<true, 8>() == cudaSuccess &&
               configure_warp<true, 6>() == cudaSuccess && configure_warp<true, 12, true>() == cudaSuccess &&
+              configure_pair<8>() == cudaSuccess &&
               cudaMalloc((void **)&f->Hn, N * sizeof(float2)) == cudaSuccess &&
               cudaFuncSetAttribute(bf_filter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES) == cudaSuccess &&
@@ -944,7 +1137,9 @@ extern "C" bf_status bf_filter_set_variant(bf_filter f, int32_t variant) {
 extern "C" int32_t bf_filter_get_variant(bf_filter f) { return f ? f->variant : -1; }
 
 // Times every variant on n_sig synthetic blocks (scratch allocated and freed
-// here) and keeps the fastest of the bit-identical two-pass variants.
+// here) in the launch form the filter uses (s declared independent or not;
+// the scratch input is never written during the timing, so independent
+// launches are correct here too) and keeps the fastest.
 extern "C" bf_status bf_filter_autotune(bf_filter f, int64_t n_sig, void *stream) {
     if (!f) return ff_fail(nullptr, BF_EINVAL, "filter is NULL");
     if (n_sig < 1 || n_sig > (1 << 20)) return ff_fail(f, BF_EINVAL, "n_sig = %lld is outside [1, 2^20]",
@@ -974,9 +1169,9 @@ extern "C" bf_status bf_filter_autotune(bf_filter f, int64_t n_sig, void *stream
     for (int v = 0; v < N_VARIANTS && e == cudaSuccess; ++v) {
         double best = 0.0;
         for (int r = 0; r < ROUNDS && e == cudaSuccess; ++r) {
-            for (int i = 0; i < WARM && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, false, v);
+            for (int i = 0; i < WARM && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, f->s_indep, v);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            for (int i = 0; i < REPS && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, false, v);
+            for (int i = 0; i < REPS && e == cudaSuccess; ++i) e = launch_filter(true, a, b, n_sig, f, s, f->s_indep, v);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -991,7 +1186,7 @@ extern "C" bf_status bf_filter_autotune(bf_filter f, int64_t n_sig, void *stream
     if (e != cudaSuccess) return ff_fail(f, BF_ECUDA, "filter autotune: %s", cudaGetErrorString(e));
     int pick = 0;
     for (int v = 1; v < N_VARIANTS; ++v)
-        if (v != 4 && us[v] < us[pick]) pick = v;  // variant 4 rounds differently
+        if (us[v] < us[pick]) pick = v;
     for (int v = 0; v < N_VARIANTS; ++v) f->tuned_us[v] = us[v];
     f->tuned_n_sig = n_sig;
     f->variant = pick;

@@ -131,8 +131,8 @@ def test_full_size_every_block(filt):
     """The bench workload (16 slots x 64 antennas x 14 symbols = 14,336 blocks)
     in the bench's launch form, every block against the oracle; the same batch
     through the 12-warp building block (the autotuner's choice at this size)
-    gives the same bits, and through the three-pass one every block is checked
-    against the oracle too."""
+    gives the same bits, and through the three-pass and two-warp ones every
+    block is checked against the oracle too."""
     b = wl.config_filter_bench().rounded()
     y = run(filt, b.h, b.s)
     ref = oracle.circular_filter(b.h, b.s)
@@ -148,6 +148,10 @@ def test_full_size_every_block(filt):
         y4 = run(filt, b.h, b.s, set_taps=False)
         worst4 = assert_per_block(y4, ref, "full size, three-pass")
         print(f"filter full size, three-pass: batch {rel(y4, ref):.3e}, worst block {worst4:.3e}")
+        bf.bf_filter_set_variant(filt, 6)
+        y6 = run(filt, b.h, b.s, set_taps=False)
+        worst6 = assert_per_block(y6, ref, "full size, two warps per block")
+        print(f"filter full size, two warps per block: batch {rel(y6, ref):.3e}, worst block {worst6:.3e}")
     finally:
         bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
 
@@ -260,15 +264,15 @@ def test_independent_input_keeps_the_y_side_ordered(filt):
 
 
 def test_variants_bit_identical_and_accurate(filt):
-    """The two-pass variants (11, 10, 8, 6 warps per CTA) give the same bits;
-    the three-pass variant rounds differently but every block stays within
-    the tolerance of the oracle."""
+    """The one-warp two-pass variants (11, 10, 8, 6 and 12 warps per CTA) give
+    the same bits; the three-pass and two-warp variants round differently but
+    every block stays within the tolerance of the oracle."""
     b = wl.config_filter_tti().rounded()  # 896 blocks
     bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
     s_d = dev_c64(b.s)
     outs = {}
     try:
-        for v in range(6):
+        for v in range(7):
             bf.bf_filter_set_variant(filt, v)
             y_d = torch.full_like(s_d, float("nan"))
             bf.bf_filter_apply(filt, s_d, b.n_sig, y_d)
@@ -277,35 +281,45 @@ def test_variants_bit_identical_and_accurate(filt):
             assert np.array_equal(outs[v].view(np.uint64), outs[0].view(np.uint64)), f"variant {v}"
         assert bf.FILTER_DEFAULT_VARIANT in (0, 1, 2, 3, 5)
         ref = oracle.circular_filter(b.h, b.s)
-        for v in (0, 4):
+        for v in (0, 4, 6):
             assert_per_block(outs[v], ref, f"variant {v}")
         with pytest.raises(bf.BfError) as ei:
-            bf.bf_filter_set_variant(filt, 6)
+            bf.bf_filter_set_variant(filt, 7)
         assert ei.value.status == bf.BF_EINVAL
     finally:
         bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
 
 
-def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
-    """Tuning picks the fastest of the bit-identical variants: results keep
-    every bit, the pick is no slower than the default when timed, and the
-    choice saves and loads on this GPU; a table from another target or of the
-    product kind is refused and leaves the filter unchanged."""
+def test_autotune_picks_fastest_accurate_and_round_trips(filt, tmp_path):
+    """Tuning picks the fastest variant: the pick is the minimum of the timed
+    variants and no slower than the default, the tuned filter gives that
+    variant's bits and every block stays within the tolerance of the oracle,
+    and the choice saves and loads on this GPU; a table from another target or
+    of the product kind is refused and leaves the filter unchanged."""
     b = wl.config_filter_tti().rounded()
     bf.bf_filter_set_taps(filt, dev_c64(b.h), len(b.h))
     s_d = dev_c64(b.s)
-    y0 = torch.empty_like(s_d)
-    bf.bf_filter_apply(filt, s_d, b.n_sig, y0)
     try:
-        v = bf.bf_filter_autotune(filt, 4096)
-        assert v in (0, 1, 2, 3, 5)
-        times = {k: bf.bf_filter_tune_query(filt, k) for k in range(6)}
-        assert all(t > 0 and n == 4096 for t, n in times.values()), times
-        assert times[v][0] <= times[bf.FILTER_DEFAULT_VARIANT][0]  # no slower than the default
+        for indep, n_tune in ((True, 112), (False, 112), (False, 4096)):
+            bf.bf_filter_set_s_independent(filt, indep)  # tuning times the launch form in use
+            v = bf.bf_filter_autotune(filt, n_tune)
+            times = {k: bf.bf_filter_tune_query(filt, k) for k in range(len(bf.FILTER_VARIANTS))}
+            assert all(t > 0 and n == n_tune for t, n in times.values()), times
+            assert times[v][0] == min(t for t, _ in times.values())
+            assert times[v][0] <= times[bf.FILTER_DEFAULT_VARIANT][0]  # no slower than the default
+            print(f"filter autotune on {n_tune} blocks ({'s independent' if indep else 'dependent'}): "
+                  f"variant {v} ({bf.FILTER_VARIANTS[v]}), "
+                  + ", ".join(f"{k}: {t:.2f}" for k, (t, _) in times.items()) + " us")
         y1 = torch.full_like(s_d, float("nan"))
         bf.bf_filter_apply(filt, s_d, b.n_sig, y1)
         torch.cuda.synchronize()
+        bf.bf_filter_set_variant(filt, v)
+        y0 = torch.empty_like(s_d)
+        bf.bf_filter_apply(filt, s_d, b.n_sig, y0)
+        torch.cuda.synchronize()
         assert torch.equal(y1.view(torch.int32), y0.view(torch.int32))
+        assert_per_block(host_c64(y1).reshape(b.n_sig, N), oracle.circular_filter(b.h, b.s), f"tuned variant {v}")
+        bf.bf_filter_set_s_independent(filt, False)
         path = str(tmp_path / "filter_tune.json")
         bf.bf_filter_tune_save(filt, path)
         other = bf.bf_filter_create(N)
@@ -332,4 +346,5 @@ def test_autotune_keeps_bits_no_slower_and_round_trips(filt, tmp_path):
         finally:
             bf.bf_filter_destroy(other)
     finally:
+        bf.bf_filter_set_s_independent(filt, False)
         bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
