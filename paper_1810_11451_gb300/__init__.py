@@ -422,7 +422,7 @@ def bf_filter_get_variant(filt) -> int:
 
 
 def bf_filter_autotune(filt, n_sig: int, stream=None) -> int:
-    """Time every variant on n_sig blocks, select the fastest bit-identical one; returns it."""
+    """Time every variant on n_sig blocks (in the launch form the filter uses), select the fastest; returns it."""
     _fcheck(_filter_sigs(lib()).bf_filter_autotune(filt, int(n_sig), _stream(stream)), filt)
     return bf_filter_get_variant(filt)
 
