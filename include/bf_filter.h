@@ -87,9 +87,11 @@ bf_status bf_filter_set_s_independent(bf_filter filter, int32_t independent);
  * The paper's optimizer picks, per size and target, the best building block
  * for an operation (Sec. IV). The filter has these blocks (variants):
  *   0 : two passes per transform (2048 = 64 x 32), one warp per block of
- *       samples, 11 warps per CTA
- *   1, 2, 3 : the same kernel with 10, 8 or 6 warps per CTA; 8 (variant 2,
- *       up to 255 registers a thread) is the default
+ *       samples, 11 warps per CTA, the spectrum read through L1
+ *   1 : the same with 10 warps per CTA
+ *   2, 3 : the same kernel with 8 or 6 warps per CTA and the spectrum in
+ *       shared memory; 8 (variant 2, up to 255 registers a thread) is the
+ *       default
  *   4 : three passes per transform (2048 = 16 x 16 x 8), 128 threads per
  *       block, 4 blocks per CTA, the next block prefetched into shared memory
  *   5 : the two-pass kernel with 12 warps per CTA, the spectrum read through

@@ -407,7 +407,8 @@ def bf_filter_set_s_independent(filt, independent: bool = True) -> None:
 
 
 FILTER_DEFAULT_VARIANT = 2  # two-pass, 8 warps per CTA
-FILTER_VARIANTS = {0: "two-pass, 11 warps per CTA", 1: "two-pass, 10 warps per CTA", 2: "two-pass, 8 warps per CTA",
+FILTER_VARIANTS = {0: "two-pass, 11 warps per CTA, spectrum through L1",
+                   1: "two-pass, 10 warps per CTA, spectrum through L1", 2: "two-pass, 8 warps per CTA",
                    3: "two-pass, 6 warps per CTA", 4: "three-pass, 4 teams of 128 threads per CTA",
                    5: "two-pass, 12 warps per CTA, spectrum through L1",
                    6: "two-pass, two warps per block, 8 blocks per CTA"}

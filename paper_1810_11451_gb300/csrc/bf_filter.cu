@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 //    of the two butterflies of a lane touches only its own column;
 //  - inverse pass A' (radix 64, Ns = 32): butterfly j = l needs inverse
 //    values (m, j), m < 64, which is row j of E, twisted by
-//    e^{+2 pi i j m / N}; that twist is applied by pass B' before its store,
-//    with the twiddles it still holds from pass B (the same values), and
-//    pass A' stores y[j + 32 q], coalesced.
+//    e^{+2 pi i j m / N}; that twist is applied by pass B' before its store
+//    (the same table values as pass B's), and pass A' stores y[j + 32 q],
+//    coalesced.
 // Both transforms run the forward DFT code: the inverse DFT of z is the
 // conjugate of the forward DFT of conj(z). So the product writes
 // conj(X H / N) (conjugation folded into the multiply), E holds conjugated
@@ -382,7 +382,7 @@ constexpr int TB_SIZE = 64 * TB_ROW;           // e^{-2 pi i a b / N}, a < 64, b
 __host__ __device__ constexpr int wsmem_bytes(int warps, bool hg = false) {
     return (TB_SIZE + (hg ? 0 : N) + warps * XBUF) * 8;
 }
-static_assert(wsmem_bytes(11) <= 232448, "11 warps per CTA exceed the shared memory of one SM");
+static_assert(wsmem_bytes(8) <= 232448, "8 warps per CTA exceed the shared memory of one SM");
 static_assert(wsmem_bytes(12, true) <= 232448, "12 warps per CTA exceed the shared memory of one SM");
 
 __host__ __device__ constexpr int padf(int e) { return e + (e >> 6); }
@@ -537,17 +537,18 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const int j = l + 32 * h;
-                // e^{-2 pi i j m / N}, m < 32: pass B's twiddles, and also the
-                // ones pass A' needs on this column's inverse outputs (value
-                // (j, q) goes to butterfly q of pass A' as its input j, twisted
-                // by e^{-2 pi i j q / N} in the conjugated domain), applied here
-                // before the store so pass A' reads its inputs ready
-                float2 tw[32], u[32];
-#pragma unroll
-                for (int m = 1; m < 32; ++m) tw[m] = TB[j * TB_ROW + m];
+                // e^{-2 pi i j m / N}, m < 32 (table row j): pass B's twiddles,
+                // and also the ones pass A' needs on this column's inverse
+                // outputs (value (j, q) goes to butterfly q of pass A' as its
+                // input j, twisted by e^{-2 pi i j q / N} in the conjugated
+                // domain), applied by pass B' before its store so pass A'
+                // reads its inputs ready. Pass B' reads them from the table
+                // again: keeping them in registers (62 more) measured no faster
+                // with 8 warps and made the 12-warp variant spill.
+                float2 u[32];
                 u[0] = E[padf(j)];
 #pragma unroll
-                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], tw[m]);
+                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
 #pragma unroll 1
                 for (int sub = 0;; ++sub) {
                     dft32(u);
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 }
                 E[padf(j)] = u[pos32(0)];
 #pragma unroll
-                for (int q2 = 1; q2 < 32; ++q2) E[padf(j + 64 * q2)] = cmul(u[pos32(q2)], tw[q2]);
+                for (int q2 = 1; q2 < 32; ++q2) E[padf(j + 64 * q2)] = cmul(u[pos32(q2)], TB[j * TB_ROW + q2]);
             }
             __syncwarp();
             // inverse pass A' input: row l of E (conjugated, already twisted)
@@ -832,8 +833,11 @@ __global__ void bf_scale_spectrum_kernel(const float2 *H, float2 *Hn) {
 }
 
 // The building blocks a filter can run (bf_filter_set_variant): the two-pass
-// kernel with 11, 10, 8 or 6 warps per CTA, or 12 with the spectrum read
-// through L1 (bit-identical results), the three-pass kernel with four
+// kernel with 11, 10 or 12 warps per CTA and the spectrum read through L1
+// (which keeps them within the 168 registers a thread that 10 to 12 warps
+// allow: read from shared memory, 10 and 11 warps spilled), or 8 or 6 warps
+// per CTA with the spectrum in shared memory (bit-identical results), the
+// three-pass kernel with four
 // 128-thread teams per CTA, and the two-pass pair kernel with eight pairs of
 // warps per CTA (variant 6).
 constexpr int N_VARIANTS = 7;
@@ -894,13 +898,13 @@ static cudaError_t launch_filter(bool filter, const float2 *s, float2 *y, long l
     if (n_sig <= 0) return cudaSuccess;
     if (!filter) return launch_warp<false, 11>(s, y, n_sig, f, st, false);
     switch (variant < 0 ? f->variant : variant) {
-        case 1: return launch_warp<true, 10>(s, y, n_sig, f, st, s_indep);
+        case 1: return launch_warp<true, 10, true>(s, y, n_sig, f, st, s_indep);
         case 2: return launch_warp<true, 8>(s, y, n_sig, f, st, s_indep);
         case 3: return launch_warp<true, 6>(s, y, n_sig, f, st, s_indep);
         case 5: return launch_warp<true, 12, true>(s, y, n_sig, f, st, s_indep);
         case 6: return launch_pair<8>(s, y, n_sig, f, st, s_indep);
         case 4: break;
-        default: return launch_warp<true, 11>(s, y, n_sig, f, st, s_indep);
+        default: return launch_warp<true, 11, true>(s, y, n_sig, f, st, s_indep);
     }
     const long long want = (n_sig + TEAMS - 1) / TEAMS;
     const int grid = (int)std::min<long long>(want, (long long)f->sm_count * CTAS_PER_SM);
@@ -955,8 +959,8 @@ extern "C" bf_status bf_filter_create(int n, bf_filter *out) {
               cudaMalloc((void **)&f->tb, TB_SIZE * sizeof(float2)) == cudaSuccess &&
               cudaMemcpy(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(f->tb, tb.data(), TB_SIZE * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-              configure_warp<false, 11>() == cudaSuccess && configure_warp<true, 11>() == cudaSuccess &&
-              configure_warp<true, 10>() == cudaSuccess && configure_warp<true, 8>() == cudaSuccess &&
+              configure_warp<false, 11>() == cudaSuccess && configure_warp<true, 11, true>() == cudaSuccess &&
+              configure_warp<true, 10, true>() == cudaSuccess && configure_warp<true, 8>() == cudaSuccess &&
               configure_warp<true, 6>() == cudaSuccess && configure_warp<true, 12, true>() == cudaSuccess &&
               configure_pair<8>() == cudaSuccess &&
               cudaMalloc((void **)&f->Hn, N * sizeof(float2)) == cudaSuccess &&
