@@ -369,11 +369,13 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 // its last DFT. The 64- and 32-point DFTs run in registers as
 // 8 x 8 and 8 x 4 splits with constant twiddles, each once in the code (two
 // loops of two rounds), so the loop body stays small. The pass twiddles come
-// from a 64 x 32 table e^{-2 pi i a b / N} (row stride 33); E has one pad per
-// 64 values, so every access of a half-warp touches 16 distinct 8-byte bank
-// pairs. The next block is copied into E (unpadded) with cp.async while the
-// current one finishes its last pass.
-constexpr int XBUF = N + N / 64;               // exchange buffer per warp
+// from a 64 x 32 table e^{-2 pi i a b / N} (row stride 33); E has two pads
+// per 64 values: the column accesses of a half-warp touch 16 distinct 8-byte
+// bank pairs, and each row starts on a 16-byte boundary, so passes A and A'
+// move a row as 16-byte pairs (conflict-free in 8-lane phases). The next block
+// is copied into E (unpadded) with cp.async while the current one finishes
+// its last pass.
+constexpr int XBUF = N + N / 32;               // exchange buffer per warp (two pads per 64 values)
 constexpr int TB_ROW = 33;
 constexpr int TB_SIZE = 64 * TB_ROW;           // e^{-2 pi i a b / N}, a < 64, b < 32, at a * 33 + b
 // shared memory of a CTA of `warps` warps (blocks in flight), one CTA per SM;
@@ -385,7 +387,17 @@ __host__ __device__ constexpr int wsmem_bytes(int warps, bool hg = false) {
 static_assert(wsmem_bytes(8) <= 232448, "8 warps per CTA exceed the shared memory of one SM");
 static_assert(wsmem_bytes(12, true) <= 232448, "12 warps per CTA exceed the shared memory of one SM");
 
-__host__ __device__ constexpr int padf(int e) { return e + (e >> 6); }
+__host__ __device__ constexpr int padf(int e) { return e + 2 * (e >> 6); }
+// Two consecutive complex values of a row of E as one 16-byte access (rows
+// start on 16-byte boundaries: 66 values apart, the buffer 16-byte aligned).
+__device__ __forceinline__ void store_pair(float2 *dst, float2 a, float2 b) {
+    *reinterpret_cast<float4 *>(dst) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void load_pair(const float2 *src, float2 &a, float2 &b) {
+    const float4 t = *reinterpret_cast<const float4 *>(src);
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+}
 
 // cos(2 pi k / 64) for k in [0, 16]
 __device__ __forceinline__ float cos64(int k) {
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
             dft64(v);
             if (round == 1 || !FILTER) break;
 #pragma unroll
-            for (int q2 = 0; q2 < 64; ++q2) E[padf(64 * l + q2)] = v[pos64(q2)];
+            for (int q2 = 0; q2 < 64; q2 += 2) store_pair(E + padf(64 * l + q2), v[pos64(q2)], v[pos64(q2 + 1)]);
             __syncwarp();
             // forward pass B, product, inverse pass B' for the lane's two columns
 #pragma unroll 1
@@ -567,7 +579,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
             __syncwarp();
             // inverse pass A' input: row l of E (conjugated, already twisted)
 #pragma unroll
-            for (int m = 0; m < 64; ++m) v[m] = E[padf(64 * l + m)];
+            for (int m = 0; m < 64; m += 2) load_pair(E + padf(64 * l + m), v[m], v[m + 1]);
             __syncwarp();  // E is free: copy the next block in while this one finishes
             if (q + stride < n_sig) stage_block(E, s + (q + stride) * N, l);
         }
@@ -584,7 +596,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
             }
         } else {  // spectrum: pass B alone, X[j + 64 q]
 #pragma unroll
-            for (int q2 = 0; q2 < 64; ++q2) E[padf(64 * l + q2)] = v[pos64(q2)];
+            for (int q2 = 0; q2 < 64; q2 += 2) store_pair(E + padf(64 * l + q2), v[pos64(q2)], v[pos64(q2 + 1)]);
             __syncwarp();
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
