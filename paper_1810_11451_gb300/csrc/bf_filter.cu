@@ -369,15 +369,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 // its last DFT. The 64- and 32-point DFTs run in registers as
 // 8 x 8 and 8 x 4 splits with constant twiddles, each once in the code (two
 // loops of two rounds), so the loop body stays small. The pass twiddles come
-// from a 64 x 32 table e^{-2 pi i a b / N} (row stride 33); E has two pads
+// from a 64 x 32 table e^{-2 pi i a b / N} (row stride 34, so a lane reads
+// its row as 16-byte pairs); E has two pads
 // per 64 values: the column accesses of a half-warp touch 16 distinct 8-byte
 // bank pairs, and each row starts on a 16-byte boundary, so passes A and A'
 // move a row as 16-byte pairs (conflict-free in 8-lane phases). The next block
 // is copied into E (unpadded) with cp.async while the current one finishes
 // its last pass.
 constexpr int XBUF = N + N / 32;               // exchange buffer per warp (two pads per 64 values)
-constexpr int TB_ROW = 33;
-constexpr int TB_SIZE = 64 * TB_ROW;           // e^{-2 pi i a b / N}, a < 64, b < 32, at a * 33 + b
+constexpr int TB_ROW = 34;  // even: rows start on 16-byte boundaries
+constexpr int TB_SIZE = 64 * TB_ROW;           // e^{-2 pi i a b / N}, a < 64, b < 32, at a * 34 + b
 // shared memory of a CTA of `warps` warps (blocks in flight), one CTA per SM;
 // with hg the spectrum is read from global memory (through L1) instead of
 // shared memory, which leaves room for more warps
@@ -560,7 +561,13 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 float2 u[32];
                 u[0] = E[padf(j)];
 #pragma unroll
-                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
+#pragma unroll
+                for (int m = 0; m < 32; m += 2) {
+                    float2 w0, w1;
+                    load_pair(TB + j * TB_ROW + m, w0, w1);
+                    if (m > 0) u[m] = cmul(E[padf(j + 64 * m)], w0);
+                    u[m + 1] = cmul(E[padf(j + 64 * (m + 1))], w1);
+                }
 #pragma unroll 1
                 for (int sub = 0;; ++sub) {
                     dft32(u);
@@ -574,7 +581,12 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 }
                 E[padf(j)] = u[pos32(0)];
 #pragma unroll
-                for (int q2 = 1; q2 < 32; ++q2) E[padf(j + 64 * q2)] = cmul(u[pos32(q2)], TB[j * TB_ROW + q2]);
+                for (int q2 = 0; q2 < 32; q2 += 2) {
+                    float2 w0, w1;
+                    load_pair(TB + j * TB_ROW + q2, w0, w1);
+                    if (q2 > 0) E[padf(j + 64 * q2)] = cmul(u[pos32(q2)], w0);
+                    E[padf(j + 64 * (q2 + 1))] = cmul(u[pos32(q2 + 1)], w1);
+                }
             }
             __syncwarp();
             // inverse pass A' input: row l of E (conjugated, already twisted)
@@ -604,7 +616,12 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 float2 u[32];
                 u[0] = E[padf(j)];
 #pragma unroll
-                for (int m = 1; m < 32; ++m) u[m] = cmul(E[padf(j + 64 * m)], TB[j * TB_ROW + m]);
+                for (int m = 0; m < 32; m += 2) {
+                    float2 w0, w1;
+                    load_pair(TB + j * TB_ROW + m, w0, w1);
+                    if (m > 0) u[m] = cmul(E[padf(j + 64 * m)], w0);
+                    u[m + 1] = cmul(E[padf(j + 64 * (m + 1))], w1);
+                }
                 dft32(u);
 #pragma unroll
                 for (int q2 = 0; q2 < 32; ++q2) yq[j + 64 * q2] = u[pos32(q2)];
@@ -698,7 +715,7 @@ __global__ void __launch_bounds__(64 * PAIRS, 1)
     // constant parts of the padded indices (see padp)
     const int e1 = 33 * L + (L >> 4);           // pass 1 writes E[e1 + q]
     const int e2 = j + 529 * r;                 // pass 2 reads E[e2 + 33 i] and E[e2 + 1058 + 33 i]
-    const int t2 = 528 * r + j;                 // and twiddles TB[t2 + 33 i], TB[t2 + 1056 + 33 i]
+    const int t2 = 544 * r + j;                 // and twiddles TB[t2 + 34 i], TB[t2 + 1088 + 34 i]
     const int e3 = 66 * j + (j >> 3) + 16 * r;  // pass 1' writes E[e3 + i] and E[e3 + 33 + i]
     const int e4 = L + wp;                      // pass 2' reads E[e4 + 66 m + (m >> 3)]
     const long long stride = (long long)gridDim.x * PAIRS;
@@ -721,8 +738,8 @@ __global__ void __launch_bounds__(64 * PAIRS, 1)
             float2 bv[16], cv[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const float2 a0 = cmul(E[e2 + 33 * i], TB[t2 + 33 * i]);
-                const float2 a1 = cmul(E[e2 + 1058 + 33 * i], TB[t2 + 1056 + 33 * i]);
+                const float2 a0 = cmul(E[e2 + 33 * i], TB[t2 + TB_ROW * i]);
+                const float2 a1 = cmul(E[e2 + 1058 + 33 * i], TB[t2 + 32 * TB_ROW + TB_ROW * i]);
                 bv[i] = cadd(a0, a1);
                 const float2 c = twc(csub(a0, a1), i);      // e^{-2 pi i i / 64}
                 cv[i] = r ? cmul_i<-1>(c) : c;              // and e^{-2 pi i 16 / 64} = -i for r = 1
@@ -761,7 +778,12 @@ __global__ void __launch_bounds__(64 * PAIRS, 1)
         // inverse pass 2: twist by the table, 32-point DFT, conjugate, store
         v[0] = E[e4];
 #pragma unroll
-        for (int m = 1; m < 32; ++m) v[m] = cmul(E[e4 + 66 * m + (m >> 3)], TB[L * TB_ROW + m]);
+        for (int m = 0; m < 32; m += 2) {
+            float2 w0, w1;
+            load_pair(TB + L * TB_ROW + m, w0, w1);
+            if (m > 0) v[m] = cmul(E[e4 + 66 * m + (m >> 3)], w0);
+            v[m + 1] = cmul(E[e4 + 66 * (m + 1) + ((m + 1) >> 3)], w1);
+        }
         pair_sync(pair);  // E is free: copy the next block in while this one finishes
         if (q + stride < n_sig) stage_block_pair(E, s + (q + stride) * N, L);
         dft32(v);
@@ -786,7 +808,7 @@ using namespace bff;
 struct bf_filter_s {
     int device = 0, sm_count = 0;
     float2 *tw = nullptr, *H = nullptr, *hpad = nullptr;
-    float2 *tb = nullptr;  // pass twiddles of the two-pass form, e^{-2 pi i a b / N} at a * 33 + b
+    float2 *tb = nullptr;  // pass twiddles of the two-pass forms, e^{-2 pi i a b / N} at a * TB_ROW + b
     float2 *Hn = nullptr;  // H / N (the spectrum scaled once, for the variant that reads it from global memory)
     bool has_taps = false;
     std::string err;
