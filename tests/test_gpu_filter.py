@@ -127,6 +127,30 @@ def test_ragged_counts(filt, n_sig):
     assert_per_block(y, ref, f"{n_sig} signals")
 
 
+_RAGGED_REFS = {}  # oracle outputs shared by the variants (same seeded signals)
+
+
+@pytest.mark.parametrize("variant", range(len(bf.FILTER_VARIANTS)))
+def test_ragged_counts_every_variant(filt, variant):
+    """Every building block on counts that leave warps, pairs or teams idle
+    (1 and 5 signals) and on one that makes them loop with a ragged last
+    round (1,001): every signal against the oracle. y starts as NaN, so a
+    block a kernel skipped fails too."""
+    b = wl.config_filter_small()
+    h = b.h.astype(np.complex64)
+    try:
+        bf.bf_filter_set_variant(filt, variant)
+        for n_sig in (1, 5, 1001):
+            rng = np.random.default_rng(1000 + n_sig)
+            s = (rng.normal(size=(n_sig, N)) + 1j * rng.normal(size=(n_sig, N))).astype(np.complex64)
+            if n_sig not in _RAGGED_REFS:
+                _RAGGED_REFS[n_sig] = oracle.circular_filter(h, s)
+            y = run(filt, h, s)
+            assert_per_block(y, _RAGGED_REFS[n_sig], f"variant {variant}, {n_sig} signals")
+    finally:
+        bf.bf_filter_set_variant(filt, bf.FILTER_DEFAULT_VARIANT)
+
+
 def test_full_size_every_block(filt):
     """The bench workload (16 slots x 64 antennas x 14 symbols = 14,336 blocks)
     in the bench's launch form, every block against the oracle; the same batch
