@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
 #pragma unroll
             for (int q2 = 0; q2 < 64; ++q2) {
                 const float2 r = v[pos64(q2)];
-                yq[l + 32 * q2] = make_float2(r.x, conj_im(r.y));
+                __stcg(yq + l + 32 * q2, make_float2(r.x, conj_im(r.y)));  // L2 only: y is not read again here
             }
         } else {  // spectrum: pass B alone, X[j + 64 q]
 #pragma unroll
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(64 * PAIRS, 1)
 #pragma unroll
         for (int q2 = 0; q2 < 32; ++q2) {
             const float2 rr = v[pos32(q2)];
-            yq[L + 64 * q2] = make_float2(rr.x, conj_im(rr.y));
+            __stcg(yq + L + 64 * q2, make_float2(rr.x, conj_im(rr.y)));  // L2 only
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
