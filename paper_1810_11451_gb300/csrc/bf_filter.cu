@@ -460,17 +460,17 @@ __device__ __forceinline__ void dft8_at(float2 (&v)[L], int b, int s) {
     for (int i = 0; i < 8; ++i) v[b + s * i] = u[i];
 }
 
-// forward 64-point DFT of v[m] (natural order); X[q1 + 8 q2] ends at v[8 q1 + q2]
+// forward 64-point DFT of v[m] (natural order) in two stages; after
+// dft64_head and the eight dft8_at(v, 8 q1, 1), X[q1 + 8 q2] ends at v[8 q1 + q2]
 __host__ __device__ constexpr int pos64(int q) { return 8 * (q & 7) + (q >> 3); }
-__device__ __forceinline__ void dft64(float2 (&v)[64]) {
+// its first stage: eight 8-point DFTs and the twiddles between the stages
+__device__ __forceinline__ void dft64_head(float2 (&v)[64]) {
 #pragma unroll
     for (int m2 = 0; m2 < 8; ++m2) dft8_at(v, m2, 8);
 #pragma unroll
     for (int m2 = 1; m2 < 8; ++m2)
 #pragma unroll
         for (int q1 = 1; q1 < 8; ++q1) v[m2 + 8 * q1] = twc(v[m2 + 8 * q1], m2 * q1);
-#pragma unroll
-    for (int q1 = 0; q1 < 8; ++q1) dft8_at(v, 8 * q1, 1);
 }
 
 // forward 32-point DFT of v[m] (natural order); X[q1 + 8 q2] ends at v[4 q1 + q2]
@@ -539,9 +539,31 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
         for (int m = 0; m < 64; ++m) v[m] = E[l + 32 * m];
         __syncwarp();  // every lane has its inputs before E is overwritten
         // Round 0: forward pass A. Round 1: inverse pass A' (conjugated).
+        float2 *yq = y + q * N;
 #pragma unroll 1
         for (int round = 0;; ++round) {
-            dft64(v);
+            // The 64-point DFT. In the inverse round (the last) the outputs
+            // of each final 8-point DFT, X[q1 + 8 q2] at v[8 q1 + q2], are
+            // stored to y as soon as they are ready, which spreads the
+            // block's stores over the computation (y = conj of pass A''s
+            // DFT, y[l + 32 q]).
+            const bool last = FILTER && round == 1;
+            if (last && !dep_done) {
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                dep_done = true;
+            }
+            dft64_head(v);
+#pragma unroll
+            for (int q1 = 0; q1 < 8; ++q1) {
+                dft8_at(v, 8 * q1, 1);
+                if (last) {
+#pragma unroll
+                    for (int q2 = 0; q2 < 8; ++q2) {
+                        const float2 r = v[8 * q1 + q2];
+                        __stcg(yq + l + 32 * (q1 + 8 * q2), make_float2(r.x, conj_im(r.y)));  // L2 only
+                    }
+                }
+            }
             if (round == 1 || !FILTER) break;
 #pragma unroll
             for (int q2 = 0; q2 < 64; q2 += 2) store_pair(E + padf(64 * l + q2), v[pos64(q2)], v[pos64(q2 + 1)]);
@@ -599,14 +621,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             dep_done = true;
         }
-        float2 *yq = y + q * N;
-        if (FILTER) {
-#pragma unroll
-            for (int q2 = 0; q2 < 64; ++q2) {
-                const float2 r = v[pos64(q2)];
-                __stcg(yq + l + 32 * q2, make_float2(r.x, conj_im(r.y)));  // L2 only: y is not read again here
-            }
-        } else {  // spectrum: pass B alone, X[j + 64 q]
+        if (!FILTER) {  // spectrum: pass B alone, X[j + 64 q]
 #pragma unroll
             for (int q2 = 0; q2 < 64; q2 += 2) store_pair(E + padf(64 * l + q2), v[pos64(q2)], v[pos64(q2 + 1)]);
             __syncwarp();
