@@ -90,17 +90,16 @@ bf_status bf_filter_set_s_independent(bf_filter filter, int32_t independent);
  *       samples, 11 warps per CTA, the spectrum read through L1
  *   1 : the same with 10 warps per CTA
  *   2, 3 : the same kernel with 8 or 6 warps per CTA and the spectrum in
- *       shared memory; 8 (variant 2, up to 255 registers a thread) is the
- *       default
+ *       shared memory (up to 255 registers a thread)
  *   4 : three passes per transform (2048 = 16 x 16 x 8), 128 threads per
  *       block, 4 blocks per CTA, the next block prefetched into shared memory
  *   5 : the two-pass kernel with 12 warps per CTA, the spectrum read through
- *       L1 instead of shared memory
+ *       L1 instead of shared memory; the default (the fastest from a few
+ *       hundred blocks up on GB300)
  *   6 : two passes per transform (2048 = 32 x 64), two warps per block,
  *       32 values a lane, 8 blocks per CTA; the radix-64 pass is split over
  *       lane pairs that exchange half their values by shuffles. A block
- *       finishes in about half the time of the one-warp kernels, which pays
- *       on small batches (one round of blocks or less)
+ *       finishes in about half the time of the one-warp kernels
  * Variants 0 to 3 and 5 give bit-identical results; variants 4 and 6 round
  * differently (other factorisations) within the same FP32 accuracy. The
  * spectrum of the taps is always computed the same way, whatever the

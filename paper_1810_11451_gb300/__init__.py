@@ -406,7 +406,7 @@ def bf_filter_set_s_independent(filt, independent: bool = True) -> None:
     _fcheck(_filter_sigs(lib()).bf_filter_set_s_independent(filt, 1 if independent else 0), filt)
 
 
-FILTER_DEFAULT_VARIANT = 2  # two-pass, 8 warps per CTA
+FILTER_DEFAULT_VARIANT = 5  # two-pass, 12 warps per CTA, spectrum through L1
 FILTER_VARIANTS = {0: "two-pass, 11 warps per CTA, spectrum through L1",
                    1: "two-pass, 10 warps per CTA, spectrum through L1", 2: "two-pass, 8 warps per CTA",
                    3: "two-pass, 6 warps per CTA", 4: "three-pass, 4 teams of 128 threads per CTA",

@@ -223,9 +223,12 @@ __device__ __forceinline__ void pass3_twiddles(float2 (&w3)[2][8], const float2 
 // One transform of the block held as v[m] = x[t + 128 m] (t = thread in the
 // team); leaves v[m] = X[t + 128 m]. E is the team's exchange buffer, tw the
 // per-pass twiddle table, w3 the thread's pass-3 twiddles.
+// With y set, pass 3 stores its outputs straight to y (element j + 256 q
+// of the transform at y[j + 256 q]) as each 8-point DFT completes, instead of
+// leaving them in v.
 template <int DIR>
 __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2 *tw, const float2 (&w3)[2][8], int t,
-                                        int team) {
+                                        int team, float2 *y = nullptr) {
     // pass 1: R = 16, Ns = 1 (no twiddles)
     dft16<DIR>(v);
 #pragma unroll
@@ -271,8 +274,13 @@ __device__ __forceinline__ void fft2048(float2 (&v)[16], float2 *E, const float2
         for (int m = 1; m < 8; ++m) u[m] = ctw<DIR>(u[m], w3[h][m]);
         dft8<DIR>(u);
         // element j + 256 q = t + 128 (h + 2 q)
+        if (y) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[h + 2 * q] = u[q];
+            for (int q = 0; q < 8; ++q) __stcg(y + j + 256 * q, u[q]);  // L2 only
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[h + 2 * q] = u[q];
+        }
     }
     team_sync(team);  // the buffer is free for the next pass 1
 }
@@ -328,18 +336,19 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
             for (int m = 0; m < 16; ++m) v[m] = sq[t + 128 * m];
         }
         fft2048<-1>(v, E, tw, w3, t, team);
-        if (FILTER) {
-#pragma unroll
-            for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], Hs[t + 128 * m]);
-            fft2048<1>(v, E, tw, w3, t, team);
-        }
         float2 *yq = y + q * N;
         if (!dep_done) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
             dep_done = true;
         }
+        if (FILTER) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) yq[t + 128 * m] = v[m];
+            for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], Hs[t + 128 * m]);
+            fft2048<1>(v, E, tw, w3, t, team, yq);  // stores y as its last pass completes
+        } else {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) yq[t + 128 * m] = v[m];
+        }
     }
 }
 
@@ -475,13 +484,17 @@ __device__ __forceinline__ void dft64_head(float2 (&v)[64]) {
 
 // forward 32-point DFT of v[m] (natural order); X[q1 + 8 q2] ends at v[4 q1 + q2]
 __host__ __device__ constexpr int pos32(int q) { return 4 * (q & 7) + (q >> 3); }
-__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+// its first stage: four 8-point DFTs and the twiddles between the stages
+__device__ __forceinline__ void dft32_head(float2 (&v)[32]) {
 #pragma unroll
     for (int m2 = 0; m2 < 4; ++m2) dft8_at(v, m2, 4);
 #pragma unroll
     for (int m2 = 1; m2 < 4; ++m2)
 #pragma unroll
         for (int q1 = 1; q1 < 8; ++q1) v[m2 + 4 * q1] = twc(v[m2 + 4 * q1], 2 * m2 * q1);
+}
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+    dft32_head(v);
 #pragma unroll
     for (int q1 = 0; q1 < 8; ++q1) dft4<-1>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
 }
@@ -801,16 +814,22 @@ __global__ void __launch_bounds__(64 * PAIRS, 1)
         }
         pair_sync(pair);  // E is free: copy the next block in while this one finishes
         if (q + stride < n_sig) stage_block_pair(E, s + (q + stride) * N, L);
-        dft32(v);
         if (!dep_done) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
             dep_done = true;
         }
+        // the 32-point DFT, each final 4-point DFT's outputs X[q1 + 8 q2]
+        // (at v[4 q1 + q2]) stored to y[L + 64 (q1 + 8 q2)] as soon as they are ready
         float2 *yq = y + q * N;
+        dft32_head(v);
 #pragma unroll
-        for (int q2 = 0; q2 < 32; ++q2) {
-            const float2 rr = v[pos32(q2)];
-            __stcg(yq + L + 64 * q2, make_float2(rr.x, conj_im(rr.y)));  // L2 only
+        for (int q1 = 0; q1 < 8; ++q1) {
+            dft4<-1>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) {
+                const float2 rr = v[4 * q1 + q2];
+                __stcg(yq + L + 64 * (q1 + 8 * q2), make_float2(rr.x, conj_im(rr.y)));  // L2 only
+            }
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -836,7 +855,7 @@ struct bf_filter_s {
     size_t slot_cap = 0;  // blocks per slot
     int slot_next = 0;    // next slot (the ring continues across calls)
     bool s_indep = false; // bf_filter_set_s_independent
-    int variant = 2;      // bf_filter_set_variant (default: 8 warps per CTA)
+    int variant = 5;      // bf_filter_set_variant (default: 12 warps per CTA, spectrum through L1)
     double tuned_us[7] = {};  // bf_filter_autotune: microseconds per launch of each variant (0: not timed)
     int64_t tuned_n_sig = 0;
     std::string device_name;

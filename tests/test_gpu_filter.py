@@ -153,10 +153,10 @@ def test_ragged_counts_every_variant(filt, variant):
 
 def test_full_size_every_block(filt):
     """The bench workload (16 slots x 64 antennas x 14 symbols = 14,336 blocks)
-    in the bench's launch form, every block against the oracle; the same batch
-    through the 12-warp building block (the autotuner's choice at this size)
-    gives the same bits, and through the three-pass and two-warp ones every
-    block is checked against the oracle too."""
+    in the bench's launch form (the default building block, 12 warps per CTA),
+    every block against the oracle; the same batch through the 8-warp building
+    block gives the same bits, and through the three-pass and two-warp ones
+    every block is checked against the oracle too."""
     b = wl.config_filter_bench().rounded()
     y = run(filt, b.h, b.s)
     ref = oracle.circular_filter(b.h, b.s)
@@ -165,9 +165,9 @@ def test_full_size_every_block(filt):
     worst = assert_per_block(y, ref, "full size")
     print(f"filter full size: batch {e:.3e}, worst block {worst:.3e}")
     try:
-        bf.bf_filter_set_variant(filt, 5)
-        y5 = run(filt, b.h, b.s, set_taps=False)
-        assert np.array_equal(y5.view(np.uint64), y.view(np.uint64))
+        bf.bf_filter_set_variant(filt, 2)
+        y2 = run(filt, b.h, b.s, set_taps=False)
+        assert np.array_equal(y2.view(np.uint64), y.view(np.uint64))
         bf.bf_filter_set_variant(filt, 4)
         y4 = run(filt, b.h, b.s, set_taps=False)
         worst4 = assert_per_block(y4, ref, "full size, three-pass")
