@@ -596,7 +596,6 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 float2 u[32];
                 u[0] = E[padf(j)];
 #pragma unroll
-#pragma unroll
                 for (int m = 0; m < 32; m += 2) {
                     float2 w0, w1;
                     load_pair(TB + j * TB_ROW + m, w0, w1);
